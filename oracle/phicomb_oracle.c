@@ -38,6 +38,7 @@
  *       max_evals evaluations.
  *   R12 s_int = max(1, ceil(s*max|t_i|)).
  *   R13 real arithmetic only; xi is searched on the real bracket [-sqrt(n) s0, sqrt(n) s0].
+ *   R14 p = 0 carries only the first block column of F (see orc_solve).
  */
 #include <math.h>
 #include <stdint.h>
@@ -477,7 +478,10 @@ int orc_solve(const orc_csr* A, int p, int r, const double* Vin, const double* t
   int k = 1;
   double sigma = 1.0;
   double c1 = INFINITY, c2 = norm_inf(D, n, w);
-  while (c1 + c2 > tol * norm_inf(S, n, w)) {
+  for (;;) {
+    const double nS = norm_inf(S, n, w);
+    if (!isfinite(c2) || !isfinite(nS)) { status = ORC_NONFINITE; break; } /* a NaN would end the test silently */
+    if (!(c1 + c2 > tol * nS)) break;
     if (k >= max_terms) { status = ORC_TERM_CAP; break; }
     k = k + 1;
     c1 = c2;
@@ -495,18 +499,20 @@ int orc_solve(const orc_csr* A, int p, int r, const double* Vin, const double* t
     }
     c2 = norm_inf(D, n, w) / sigma;
     for (int64_t idx = 0; idx < (int64_t)n * w; ++idx) S[idx] = S[idx] + D[idx] / sigma;
-    if (!isfinite(c2)) { status = ORC_NONFINITE; break; }
   }
   st->series_terms = k;
 
-  /* ---- F = S(:, [1:r, pr+1:(p+1)r]) ;  F(:,1:r) <- A F(:,1:r) T + v0 1^T ---- */
-  const int wf = 2 * r;
+  /* ---- F = S(:, [1:r, pr+1:(p+1)r]) ;  F(:,1:r) <- A F(:,1:r) T + v0 1^T ----
+   * Reading R14: with p = 0 (only v0 given, the output option e^{tA} v0 of Section 4) both block
+   * columns are column block 0, the second copy never reaches the output, and only the first block
+   * is carried (its norms alone enter the truncation test). */
+  const int wf = (p == 0) ? r : 2 * r;
   double* F = (double*)malloc(sizeof(double) * (size_t)n * wf);
   double* E = (double*)malloc(sizeof(double) * (size_t)n * wf);
   double* Yf = (double*)malloc(sizeof(double) * (size_t)n * wf);
   for (int i = 0; i < r; ++i) {
     memcpy(F + (int64_t)i * n, S + (int64_t)i * n, sizeof(double) * (size_t)n);
-    memcpy(F + (int64_t)(r + i) * n, S + (int64_t)(p * r + i) * n, sizeof(double) * (size_t)n);
+    if (p > 0) memcpy(F + (int64_t)(r + i) * n, S + (int64_t)(p * r + i) * n, sizeof(double) * (size_t)n);
   }
   if (status == ORC_OK) {
     csr_times_block(A, F, r, Yf);
@@ -522,7 +528,10 @@ int orc_solve(const orc_csr* A, int p, int r, const double* Vin, const double* t
     memcpy(E, F, sizeof(double) * (size_t)n * wf);
     int kk = 0;
     double d1 = INFINITY, d2 = norm_inf(F, n, wf);
-    while (d1 + d2 > tol * norm_inf(E, n, wf)) {
+    for (;;) {
+      const double nE = norm_inf(E, n, wf);
+      if (!isfinite(d2) || !isfinite(nE)) { status = ORC_NONFINITE; break; }
+      if (!(d1 + d2 > tol * nE)) break;
       if (kk >= max_terms) { status = ORC_TERM_CAP; break; }
       kk = kk + 1;
       d1 = d2;
@@ -537,7 +546,6 @@ int orc_solve(const orc_csr* A, int p, int r, const double* Vin, const double* t
       }
       d2 = norm_inf(F, n, wf);
       for (int64_t idx = 0; idx < (int64_t)n * wf; ++idx) E[idx] = E[idx] + F[idx];
-      if (!isfinite(d2)) { status = ORC_NONFINITE; break; }
     }
     st->recovery_terms += kk;
     if (kk > st->max_inner_terms) st->max_inner_terms = kk;
@@ -551,7 +559,7 @@ int orc_solve(const orc_csr* A, int p, int r, const double* Vin, const double* t
     for (int i = 0; i < r; ++i) {       /* F <- E + S(:, [blk 0, blk p]) ; F(:,1:r) <- E(:,1:r) */
       for (int64_t q = 0; q < n; ++q) {
         F[(int64_t)i * n + q] = E[(int64_t)i * n + q];
-        F[(int64_t)(r + i) * n + q] = E[(int64_t)(r + i) * n + q] + S[(int64_t)(p * r + i) * n + q];
+        if (p > 0) F[(int64_t)(r + i) * n + q] = E[(int64_t)(r + i) * n + q] + S[(int64_t)(p * r + i) * n + q];
       }
     }
   }
@@ -620,7 +628,10 @@ int orc_solve_single(const orc_csr* A, int p, const double* Vin, double t, doubl
   int status = ORC_OK;
   int k = 1;
   double sigma = 1.0, c1 = INFINITY, c2 = norm_inf(D, n, P);
-  while (c1 + c2 > tol * norm_inf(S, n, P)) {
+  for (;;) {
+    const double nS = norm_inf(S, n, P);
+    if (!isfinite(c2) || !isfinite(nS)) { status = ORC_NONFINITE; break; }
+    if (!(c1 + c2 > tol * nS)) break;
     if (k >= max_terms) { status = ORC_TERM_CAP; break; }
     k++;
     c1 = c2;
@@ -632,7 +643,6 @@ int orc_solve_single(const orc_csr* A, int p, const double* Vin, double t, doubl
     for (int64_t idx = 0; idx < (int64_t)n * P; ++idx) D[idx] = t * (Y[idx] - xi * D[idx]) / (double)s_int + Vb[idx];
     c2 = norm_inf(D, n, P) / sigma;
     for (int64_t idx = 0; idx < (int64_t)n * P; ++idx) S[idx] = S[idx] + D[idx] / sigma;
-    if (!isfinite(c2)) { status = ORC_NONFINITE; break; }
   }
   st->series_terms = k;
   double* F = (double*)malloc(sizeof(double) * (size_t)n * 2);
@@ -650,7 +660,10 @@ int orc_solve_single(const orc_csr* A, int p, const double* Vin, double t, doubl
     memcpy(E, F, sizeof(double) * (size_t)n * 2);
     int kk = 0;
     double d1 = INFINITY, d2 = norm_inf(F, n, 2);
-    while (d1 + d2 > tol * norm_inf(E, n, 2)) {
+    for (;;) {
+      const double nE = norm_inf(E, n, 2);
+      if (!isfinite(d2) || !isfinite(nE)) { status = ORC_NONFINITE; break; }
+      if (!(d1 + d2 > tol * nE)) break;
       if (kk >= max_terms) { status = ORC_TERM_CAP; break; }
       kk++;
       d1 = d2;
@@ -659,7 +672,6 @@ int orc_solve_single(const orc_csr* A, int p, const double* Vin, double t, doubl
       for (int64_t idx = 0; idx < n * 2; ++idx) F[idx] = t * (Yf[idx] - xi * F[idx]) / ((double)s_int * kk);
       d2 = norm_inf(F, n, 2);
       for (int64_t idx = 0; idx < n * 2; ++idx) E[idx] = E[idx] + F[idx];
-      if (!isfinite(d2)) { status = ORC_NONFINITE; break; }
     }
     st->recovery_terms += kk;
     if (kk > st->max_inner_terms) st->max_inner_terms = kk;

@@ -1,0 +1,104 @@
+"""ctypes binding of the C ABI declared in ``include/phicomb.h`` (same names, argument marshalling only).
+
+The shared library is built in-tree by :mod:`paper_2509_26475_gb300.build`; loading fails loudly when
+it is missing.  There is no fallback: every step of the method runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+PHIC_OK, PHIC_INVALID_ARG, PHIC_NONFINITE, PHIC_TERM_CAP, PHIC_TIMEOUT, PHIC_CUDA_ERROR, PHIC_WORKSPACE_TOO_SMALL = range(7)
+PHIC_F64, PHIC_F32 = 0, 1
+PHIC_NO_V0 = 1
+PHIC_PHASE_SERIES, PHIC_PHASE_RECOVER = 0x10, 0x20
+PHIC_MAX_R, PHIC_MAX_P, PHIC_MAX_WIDTH = 16, 15, 128
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "TERM_CAP", 4: "TIMEOUT", 5: "CUDA_ERROR",
+                6: "WORKSPACE_TOO_SMALL"}
+
+
+class PhicError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: phicomb status {STATUS_NAMES.get(int(status), status)}")
+
+
+class phic_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p), ("prec", ctypes.c_int32)]
+
+
+class phic_select_opts(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("max_evals", ctypes.c_int32), ("spin_limit_ms", ctypes.c_double)]
+
+
+class phic_params(ctypes.Structure):
+    _fields_ = [("xi", ctypes.c_double), ("s", ctypes.c_double), ("s0", ctypes.c_double),
+                ("f_star", ctypes.c_double), ("r", ctypes.c_int32), ("evals", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class phic_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("s_int", ctypes.c_int32), ("series_terms", ctypes.c_int32),
+                ("max_inner_terms", ctypes.c_int32), ("recovery_terms", ctypes.c_int64),
+                ("spmm_count", ctypes.c_int64), ("xi", ctypes.c_double), ("s", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) for every function declared in include/phicomb.h
+_P = ctypes.c_void_p
+SIGNATURES = [
+    ("phic_select_opts_default", None, [ctypes.POINTER(phic_select_opts)]),
+    ("phic_select_workspace_size", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    ("phic_select_params", ctypes.c_int, [ctypes.POINTER(phic_csr), ctypes.POINTER(phic_select_opts), _P, _P,
+                                          ctypes.c_size_t, _P, _P]),
+    ("phic_params_set", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P]),
+    ("phic_solve_workspace_size", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+    ("phic_solve", ctypes.c_int, [ctypes.POINTER(phic_csr), ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
+                                  ctypes.c_double, _P, ctypes.c_uint32, ctypes.c_int32, _P, _P, ctypes.c_size_t, _P,
+                                  ctypes.c_int32, _P]),
+    ("phic_set_spin_limit_ms", None, [ctypes.c_double]),
+    ("phic_set_blocks_per_sm", None, [ctypes.c_int32]),
+    ("phic_set_test_fault", None, [ctypes.c_int32]),
+    ("phic_status_string", ctypes.c_char_p, [ctypes.c_int32]),
+    ("phic_launch_count", ctypes.c_uint64, []),
+    ("phic_version", ctypes.c_int32, []),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libphicomb.so (optionally building it first); raises if it is not there."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if build_if_missing:
+                _build.build()
+            else:
+                raise RuntimeError(f"{_build.LIB} is missing: build it with __graft_entry__.build() "
+                                   "(nvcc, sm_103a); there is no CPU fallback")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def check(status: int, where: str):
+    if int(status) != PHIC_OK:
+        raise PhicError(status, where)

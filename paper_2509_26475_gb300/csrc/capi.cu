@@ -1,0 +1,234 @@
+// C ABI of the phicomb library: argument checks, workspace layout and kernel launches.
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "phicomb.h"
+
+namespace phic {
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+std::atomic<long long> g_spin_ns{2000000000LL};
+std::atomic<int> g_blocks_per_sm{0};
+std::atomic<int> g_fault{0};
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) % kAlign) == 0; }
+
+bool csr_ok(const phic_csr* A) {
+  if (!A) return false;
+  if (A->n < 1 || A->n >= (int64_t)INT32_MAX || A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX) return false;
+  if (!A->rowptr) return false;
+  if (A->nnz > 0 && (!A->colidx || !A->values)) return false;
+  if (A->prec != PHIC_F64 && A->prec != PHIC_F32) return false;
+  return true;
+}
+
+struct SelectLayout {
+  size_t ctl, part, basis, total;
+};
+SelectLayout select_layout(int64_t n, int m) {
+  SelectLayout L;
+  L.ctl = 0;
+  L.part = align_up(sizeof(Ctl));
+  L.basis = L.part + align_up((size_t)2 * max_select_grid() * 16);
+  L.total = L.basis + align_up((size_t)n * (size_t)(m + 1) * sizeof(double));
+  return L;
+}
+
+struct SolveLayout {
+  size_t ctlS, ctlR, state, Vt[2], Dt[2], S, Ft[2], E, total;
+  TileLayout sl, fl;
+};
+SolveLayout solve_layout(int64_t n, int p, int r, int prec) {
+  SolveLayout L;
+  const size_t es = prec == PHIC_F32 ? 4 : 8;
+  L.sl = pick_layout((p + 1) * r);
+  L.fl = pick_layout(p == 0 ? r : 2 * r);
+  const size_t tileS = align_up((size_t)n * L.sl.ws * es);
+  const size_t tileF = align_up((size_t)n * L.fl.ws * es);
+  size_t off = 0;
+  L.ctlS = off; off += align_up(sizeof(Ctl));
+  L.ctlR = off; off += align_up(sizeof(Ctl));
+  L.state = off; off += align_up(sizeof(SolveState));
+  for (int q = 0; q < 2; ++q) { L.Vt[q] = off; off += tileS; }
+  for (int q = 0; q < 2; ++q) { L.Dt[q] = off; off += tileS; }
+  L.S = off; off += tileS;
+  for (int q = 0; q < 2; ++q) { L.Ft[q] = off; off += tileF; }
+  L.E = off; off += tileF;
+  L.total = off;
+  return L;
+}
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int blocks_per_sm(int elem_bytes) {
+  (void)elem_bytes;
+  const int b = g_blocks_per_sm.load();
+  return b > 0 ? b : 4;
+}
+
+}  // namespace phic
+
+using namespace phic;
+
+extern "C" {
+
+void phic_select_opts_default(phic_select_opts* o) {
+  if (!o) return;
+  o->m = 61;
+  o->tol = std::ldexp(1.0, -53);
+  o->delta = 0.8;
+  o->seed = 0x5EEDull;
+  o->max_evals = 200;
+  o->spin_limit_ms = 2000.0;
+}
+
+phic_status phic_select_workspace_size(int64_t n, int32_t m, size_t* bytes) {
+  if (!bytes || n < 1 || n >= (int64_t)INT32_MAX || m < 1 || m > 128) return PHIC_INVALID_ARG;
+  *bytes = select_layout(n, m).total;
+  return PHIC_OK;
+}
+
+phic_status phic_select_params(const phic_csr* A, const phic_select_opts* opts, const double* v, void* ws,
+                               size_t ws_bytes, phic_params* params_dev, phic_stream_t stream) {
+  phic_select_opts o;
+  if (opts) o = *opts; else phic_select_opts_default(&o);
+  if (!csr_ok(A) || !params_dev || !ws || !aligned(ws)) return PHIC_INVALID_ARG;
+  if (o.m < 1 || o.m > 128 || !(o.tol > 0.0) || !std::isfinite(o.tol) || !(o.delta > 0.0) || !(o.delta <= 1.0) ||
+      o.max_evals < 1 || !(o.spin_limit_ms > 0.0))
+    return PHIC_INVALID_ARG;
+  const SelectLayout L = select_layout(A->n, o.m);
+  if (ws_bytes < L.total) return PHIC_WORKSPACE_TOO_SMALL;
+  char* base = static_cast<char*>(ws);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(base + L.ctl, 0, sizeof(Ctl), st) != cudaSuccess) return PHIC_CUDA_ERROR;
+  SelectArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = (int)A->n;
+  a.nnz = (int)A->nnz;
+  a.rowptr = A->rowptr;
+  a.colidx = A->colidx;
+  a.vals = A->values;
+  a.vals_f32 = A->prec == PHIC_F32;
+  a.v = v;
+  a.seed = o.seed;
+  a.m = o.m;
+  a.tol = o.tol;
+  a.delta = o.delta;
+  a.max_evals = o.max_evals;
+  a.Vb = reinterpret_cast<double*>(base + L.basis);
+  a.part = base + L.part;
+  a.ctl = reinterpret_cast<Ctl*>(base + L.ctl);
+  a.out = params_dev;
+  a.spin_ns = (unsigned long long)(o.spin_limit_ms * 1e6);
+  return launch_select(a, st, nullptr) == cudaSuccess ? PHIC_OK : PHIC_CUDA_ERROR;
+}
+
+phic_status phic_params_set(phic_params* params_dev, double xi, double s, phic_stream_t stream) {
+  if (!params_dev || !std::isfinite(xi) || !(s >= 0.0) || !std::isfinite(s)) return PHIC_INVALID_ARG;
+  return launch_params_set(params_dev, xi, s, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? PHIC_OK : PHIC_CUDA_ERROR;
+}
+
+phic_status phic_solve_workspace_size(int64_t n, int32_t p, int32_t r, int32_t prec, size_t* bytes) {
+  if (!bytes || n < 1 || n >= (int64_t)INT32_MAX || p < 0 || p > PHIC_MAX_P || r < 1 || r > PHIC_MAX_R ||
+      (p + 1) * r > PHIC_MAX_WIDTH || (prec != PHIC_F64 && prec != PHIC_F32))
+    return PHIC_INVALID_ARG;
+  *bytes = solve_layout(n, p, r, prec).total;
+  return PHIC_OK;
+}
+
+phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, const double* t, const double* alpha,
+                       double tol, const phic_params* params_dev, uint32_t flags, int32_t max_terms, void* W, void* ws,
+                       size_t ws_bytes, phic_stats* stats_dev, int32_t prec, phic_stream_t stream) {
+  if (!csr_ok(A) || A->prec != prec || !V || !W || !t || !alpha || !params_dev || !ws || !aligned(ws))
+    return PHIC_INVALID_ARG;
+  if (p < 0 || p > PHIC_MAX_P || r < 1 || r > PHIC_MAX_R || (p + 1) * r > PHIC_MAX_WIDTH) return PHIC_INVALID_ARG;
+  if (!(tol > 0.0) || !std::isfinite(tol)) return PHIC_INVALID_ARG;
+  if ((flags & ~(PHIC_NO_V0 | PHIC_PHASE_SERIES | PHIC_PHASE_RECOVER)) != 0 || ((flags & PHIC_NO_V0) && p == 0))
+    return PHIC_INVALID_ARG;
+  bool run_series = true, run_recover = true;
+  if (flags & (PHIC_PHASE_SERIES | PHIC_PHASE_RECOVER)) {
+    run_series = (flags & PHIC_PHASE_SERIES) != 0;
+    run_recover = (flags & PHIC_PHASE_RECOVER) != 0;
+  }
+  for (int i = 0; i < r; ++i)
+    if (!std::isfinite(t[i]) || !std::isfinite(alpha[i])) return PHIC_INVALID_ARG;
+  const SolveLayout L = solve_layout(A->n, p, r, prec);
+  if (ws_bytes < L.total) return PHIC_WORKSPACE_TOO_SMALL;
+  char* base = static_cast<char*>(ws);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (run_series && cudaMemsetAsync(base, 0, L.Vt[0], st) != cudaSuccess) return PHIC_CUDA_ERROR;  // control + state
+  SolveArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = (int)A->n;
+  a.nnz = (int)A->nnz;
+  a.rowptr = A->rowptr;
+  a.colidx = A->colidx;
+  a.vals = A->values;
+  a.Vin = V;
+  a.W = W;
+  a.p = p;
+  a.r = r;
+  a.no_v0 = (flags & PHIC_NO_V0) ? 1 : 0;
+  a.S_lay = L.sl;
+  a.F_lay = L.fl;
+  for (int i = 0; i < r; ++i) {
+    a.t[i] = t[i];
+    a.alpha[i] = alpha[i];
+  }
+  a.tol = tol;
+  a.max_terms = max_terms > 0 ? max_terms : 610;
+  a.params = params_dev;
+  for (int q = 0; q < 2; ++q) {
+    a.Vt[q] = base + L.Vt[q];
+    a.Dt[q] = base + L.Dt[q];
+    a.Ft[q] = base + L.Ft[q];
+  }
+  a.S = base + L.S;
+  a.E = base + L.E;
+  a.ctlS = reinterpret_cast<Ctl*>(base + L.ctlS);
+  a.ctlR = reinterpret_cast<Ctl*>(base + L.ctlR);
+  a.state = reinterpret_cast<SolveState*>(base + L.state);
+  a.stats = stats_dev;
+  a.spin_ns = (unsigned long long)g_spin_ns.load();
+  a.fault = g_fault.exchange(0);
+  if (run_series && launch_series(a, prec, st, nullptr) != cudaSuccess) return PHIC_CUDA_ERROR;
+  if (run_recover && launch_recover(a, prec, st, nullptr) != cudaSuccess) return PHIC_CUDA_ERROR;
+  return PHIC_OK;
+}
+
+void phic_set_spin_limit_ms(double ms) {
+  if (ms > 0.0 && std::isfinite(ms)) g_spin_ns.store((long long)(ms * 1e6));
+}
+
+void phic_set_blocks_per_sm(int32_t blocks) { g_blocks_per_sm.store(blocks > 0 ? blocks : 0); }
+
+void phic_set_test_fault(int32_t mode) { g_fault.store(mode == 1 ? 1 : 0); }
+
+const char* phic_status_string(int32_t s) {
+  switch (s) {
+    case PHIC_OK: return "ok";
+    case PHIC_INVALID_ARG: return "invalid argument";
+    case PHIC_NONFINITE: return "non-finite norm";
+    case PHIC_TERM_CAP: return "Taylor term cap reached";
+    case PHIC_TIMEOUT: return "grid barrier wait timed out";
+    case PHIC_CUDA_ERROR: return "CUDA runtime error";
+    case PHIC_WORKSPACE_TOO_SMALL: return "workspace too small";
+    default: return "unknown status";
+  }
+}
+
+uint64_t phic_launch_count(void) { return g_launches.load(); }
+
+int32_t phic_version(void) { return 100; }
+
+}  // extern "C"

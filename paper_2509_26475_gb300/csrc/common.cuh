@@ -1,0 +1,250 @@
+// Device helpers shared by the phicomb kernels: bounded grid barrier, cross-block max slots,
+// scaled sums of squares and vector loads for the row-major block tiles.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "phicomb.h"
+
+namespace phic {
+
+constexpr int kBlock = 256;  // threads per block of every persistent kernel
+
+// Control block at the head of each persistent kernel's workspace region; zeroed before launch.
+struct __align__(256) Ctl {
+  unsigned bar_count;  // arrivals at the current grid barrier
+  unsigned bar_gen;    // completed grid barriers
+  int status;          // first phic_status != OK seen by any block
+  int fault;           // test hook: block 0 leaves before its first barrier when set
+  unsigned long long slot[4][4];  // max-reduction slots (bit patterns of non-negative doubles), by phase % 4
+  double pad[12];
+};
+static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte line");
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void set_status(Ctl* c, int st) { atomicCAS(&c->status, 0, st); }
+
+__device__ __forceinline__ int read_status(const Ctl* c) { return *(volatile const int*)&c->status; }
+
+// Grid-wide barrier of a cooperative launch.  Every thread of every block calls it.  A wait longer
+// than spin_ns sets PHIC_TIMEOUT and returns false in every thread of the block that gave up; the
+// caller then leaves the kernel, so no block ever waits without bound.  Writes made before the
+// barrier by any thread of the grid are visible after it (block barrier + gpu-scope fences).
+__device__ __forceinline__ bool grid_sync(Ctl* c, unsigned long long spin_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (gridDim.x > 1) {
+      volatile unsigned* gen = &c->bar_gen;
+      const unsigned g = *gen;
+      __threadfence();
+      const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(&c->bar_count, 0u);
+        __threadfence();
+        atomicAdd(&c->bar_gen, 1u);
+      } else {
+        const unsigned long long t0 = global_ns();
+        unsigned spins = 0;
+        while (*gen == g) {
+          if ((++spins & 63u) == 0 && global_ns() - t0 > spin_ns) {
+            ok = 0;
+            set_status(c, PHIC_TIMEOUT);
+            break;
+          }
+        }
+      }
+      __threadfence();
+    } else {
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---- max over the grid of non-negative doubles, carried as their bit patterns --------------------
+// Non-negative doubles order like their unsigned bit patterns; NaN and Inf patterns sort above every
+// finite value, so a non-finite norm anywhere surfaces in the slot.
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(unsigned long long u) { return __longlong_as_double((long long)u); }
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Block-wide max of per-thread values; the result is valid in thread 0.
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v) {
+  __shared__ unsigned long long s_w[kBlock / 32];
+  v = warp_max_u64(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) s_w[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < kBlock / 32 ? s_w[lane] : 0ull;
+    v = warp_max_u64(v);
+  }
+  return v;
+}
+
+__device__ __forceinline__ void slot_reset(Ctl* c, int phase) {
+  if (blockIdx.x == 0 && threadIdx.x < 4) c->slot[(phase + 2) & 3][threadIdx.x] = 0ull;
+}
+__device__ __forceinline__ void slot_max(Ctl* c, int phase, int idx, unsigned long long v) {
+  atomicMax(&c->slot[phase & 3][idx], v);
+}
+__device__ __forceinline__ double slot_get(const Ctl* c, int phase, int idx) {
+  return bitsd(*(volatile const unsigned long long*)&c->slot[phase & 3][idx]);
+}
+
+// ---- scaled sum of squares: value = ssq * 2^(2e) ------------------------------------------------
+struct Ssq {
+  int e;
+  double ssq;
+};
+constexpr int kSsqEmpty = -4000;
+
+__device__ __forceinline__ Ssq ssq_empty() { return Ssq{kSsqEmpty, 0.0}; }
+
+__device__ __forceinline__ void ssq_add(Ssq& a, double x) {
+  if (x == 0.0) return;
+  if (!isfinite(x)) {  // keep Inf/NaN visible
+    a.e = 5000;
+    a.ssq = (double)NAN;
+    return;
+  }
+  if (a.e >= 5000) return;
+  int ex = ilogb(x);
+  if (ex < -1022) ex = -1022;
+  if (ex > a.e) {
+    a.ssq = (a.e == kSsqEmpty) ? 0.0 : scalbn(a.ssq, 2 * (a.e - ex));
+    a.e = ex;
+  }
+  const double y = scalbn(x, -a.e);
+  a.ssq = fma(y, y, a.ssq);
+}
+
+__device__ __forceinline__ Ssq ssq_combine(Ssq a, Ssq b) {
+  if (a.e == kSsqEmpty) return b;
+  if (b.e == kSsqEmpty) return a;
+  if (a.e >= 5000 || b.e >= 5000) return Ssq{5000, (double)NAN};
+  const int e = a.e > b.e ? a.e : b.e;
+  return Ssq{e, scalbn(a.ssq, 2 * (a.e - e)) + scalbn(b.ssq, 2 * (b.e - e))};
+}
+
+// log of the 2-norm; -inf for a zero vector, NaN when a non-finite value was seen.
+__device__ __forceinline__ double ssq_log_norm(Ssq a) {
+  if (a.e == kSsqEmpty || a.ssq == 0.0) return -INFINITY;
+  if (a.e >= 5000) return (double)NAN;
+  return (double)a.e * 0.69314718055994530942 + 0.5 * log(a.ssq);
+}
+
+__device__ __forceinline__ Ssq warp_ssq(Ssq a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Ssq b;
+    b.e = __shfl_xor_sync(0xffffffffu, a.e, o);
+    b.ssq = __shfl_xor_sync(0xffffffffu, a.ssq, o);
+    a = ssq_combine(a, b);
+  }
+  return a;
+}
+
+// Block-wide combine; the result is valid in thread 0.
+__device__ __forceinline__ Ssq block_ssq(Ssq a) {
+  __shared__ int s_e[kBlock / 32];
+  __shared__ double s_s[kBlock / 32];
+  a = warp_ssq(a);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    s_e[wid] = a.e;
+    s_s[wid] = a.ssq;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    a = lane < kBlock / 32 ? Ssq{s_e[lane], s_s[lane]} : ssq_empty();
+    a = warp_ssq(a);
+  }
+  return a;
+}
+
+// ---- vector loads/stores of CW consecutive elements (the tiles keep them aligned) ----------------
+template <typename T, int CW>
+struct VecIO;
+
+template <>
+struct VecIO<double, 1> {
+  static __device__ __forceinline__ void ld(const double* p, double (&x)[1]) { x[0] = *p; }
+  static __device__ __forceinline__ void st(double* p, const double (&x)[1]) { *p = x[0]; }
+};
+template <>
+struct VecIO<double, 2> {
+  static __device__ __forceinline__ void ld(const double* p, double (&x)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    x[0] = v.x; x[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(double* p, const double (&x)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+  }
+};
+template <>
+struct VecIO<double, 4> {
+  static __device__ __forceinline__ void ld(const double* p, double (&x)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+  }
+  static __device__ __forceinline__ void st(double* p, const double (&x)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
+  }
+};
+template <>
+struct VecIO<float, 1> {
+  static __device__ __forceinline__ void ld(const float* p, float (&x)[1]) { x[0] = *p; }
+  static __device__ __forceinline__ void st(float* p, const float (&x)[1]) { *p = x[0]; }
+};
+template <>
+struct VecIO<float, 2> {
+  static __device__ __forceinline__ void ld(const float* p, float (&x)[2]) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    x[0] = v.x; x[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(float* p, const float (&x)[2]) {
+    *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+  }
+};
+template <>
+struct VecIO<float, 4> {
+  static __device__ __forceinline__ void ld(const float* p, float (&x)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  }
+  static __device__ __forceinline__ void st(float* p, const float (&x)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  }
+};
+
+// Sum over the lanes of one row group (Lp2 consecutive lanes, a power of two <= 32, aligned).
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int Lp2) {
+  for (int o = 1; o < Lp2; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace phic

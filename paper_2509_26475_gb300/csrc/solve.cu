@@ -1,0 +1,696 @@
+// Algorithm 3 of the paper (Section 4): block scaling-and-recovering truncated Taylor method for
+// w_i = sum_j alpha_i^j phi_j(t_i A) v_j, i = 1..r.
+//
+// Two persistent cooperative kernels share one workspace:
+//   series_kernel   -- setup, then the block series S = sum_k D_k / k! of Theorem 1 (eq. rec.D with
+//                      the shift of eq. cD.shift), term by term with the truncation test (3.3).
+//   recover_kernel  -- the first-block recovery F(:,1:r) <- A F(:,1:r) T + v0 1^T, the s-1 recovery
+//                      steps of eq. rec.F.shift (Taylor series of exp(A_1 T/s) with the same test, the
+//                      undo factor mu and the refresh from S), and the output w_i = F_i + alpha_i F_{r+i}.
+// The data-dependent loops never return to the host: every Taylor term ends at a bounded grid barrier
+// after which thread 0 of every block reads the same grid-wide norms, takes the same branch and
+// broadcasts it to its block.
+//
+// Tiles are row-major: row i of an n x w block is w consecutive values at row stride ws (see
+// pick_layout).  Each row is processed by L lanes of CW columns; the lanes of a row are consecutive in
+// a warp, so the row sums of |x| for the infinity norm are shuffle reductions.  A thread keeps the
+// same lane in every pass (the grid stride is a multiple of the block size, itself a multiple of the
+// lane group), so its per-column constants live in registers.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace phic {
+
+namespace {
+
+// Items (row, lane) of one pass; the bound is uniform across each block so that the shuffles inside
+// the body always see full warps.
+struct ItemLoop {
+  long long total;  // n * Lp2 rounded up to a multiple of the block size
+  int shift;        // log2(Lp2)
+  __device__ ItemLoop(int n, int Lp2) {
+    shift = __ffs(Lp2) - 1;
+    const long long items = (long long)n << shift;
+    total = (items + kBlock - 1) / kBlock * kBlock;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+__device__ __forceinline__ void umax(unsigned long long& m, double v) {
+  const unsigned long long u = dbits(v);
+  m = u > m ? u : m;
+}
+
+// acc[j] += sum_q A(row, col_q) X(col_q, c0 + j) over the row's nonzeros; flags a bad column index
+// and skips it, so no address outside X is read.
+template <typename T, int CW>
+__device__ __forceinline__ void spmm_row(const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                                         const T* __restrict__ vals, const T* __restrict__ X, int ws, int c0,
+                                         int row, int n, T (&acc)[CW], int& bad) {
+  const int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
+  for (int q = beg; q < end; ++q) {
+    const int col = __ldg(colidx + q);
+    const T av = __ldg(vals + q);
+    if ((unsigned)col >= (unsigned)n) {
+      bad = 1;
+      continue;
+    }
+    T x[CW];
+    VecIO<T, CW>::ld(X + (size_t)col * ws + c0, x);
+#pragma unroll
+    for (int j = 0; j < CW; ++j) acc[j] = fma(av, x[j], acc[j]);
+  }
+}
+
+// Block-level broadcast of the loop decision made by thread 0.
+struct LoopCtl {
+  int go;            // 1: run another term
+  int k;             // index of the term to run
+  int status;
+};
+
+// Per-term column coefficients of the series, already divided by k (see series_kernel).
+template <typename T>
+struct SeriesTerm {
+  T kd[PHIC_MAX_R], ka[PHIC_MAX_R], kt[PHIC_MAX_R];
+};
+
+struct SeriesScalars {
+  double xi, tc[PHIC_MAX_R], cA[PHIC_MAX_R], cD[PHIC_MAX_R], cV[PHIC_MAX_R];
+  int s_int, bad;
+};
+
+struct RecoverScalars {
+  double xi, tcF[PHIC_MAX_R], mu[PHIC_MAX_R], scale[PHIC_MAX_R];
+  double cj[PHIC_MAX_P + 1][PHIC_MAX_R];
+  int s_int, series_terms, status;
+};
+
+}  // namespace
+
+// ===================================================================================================
+// Block series (Algorithm 3: setup and the first while loop)
+// ===================================================================================================
+// The recurrence is carried divided by k!: with X = A_1 (I kron T/s),
+//   V~_k = V~_{k-1} Jsh / k,   D~_k = X D~_{k-1} / k + V~_k,   S = sum_k D~_k,   c2 = ||D~_k||_inf,
+// which equals the paper's D_k / k! and V_k / k! term by term but never holds the growing X^k D_1,
+// which would overflow FP32 (and, for a large ||X||, FP64) long before the terms become small.
+template <typename T, int CW>
+__global__ void __launch_bounds__(kBlock) series_kernel(const SolveArgs a) {
+  __shared__ SeriesScalars sc;
+  __shared__ LoopCtl lc;
+  __shared__ SeriesTerm<T> tk;
+  Ctl* ctl = a.ctlS;
+  const int n = a.n, r = a.r, p = a.p;
+  const TileLayout L = a.S_lay;
+
+  if (threadIdx.x == 0) {
+    // s <- ceil(s max|t_i|);  mu = exp((xi/s) T);  V <- V (I kron 1^T mu/s);
+    // Jsh = (J kron Delta - xi I kron T)/s  (divided by s as in Algorithm 2)
+    const double xi = a.params->xi, s = a.params->s;
+    int bad = !isfinite(xi) || !(s >= 0.0) || !isfinite(s);
+    double tmax = 0.0;
+    for (int i = 0; i < r; ++i) tmax = fmax(tmax, fabs(a.t[i]));
+    double sint = ceil(s * tmax);
+    if (!(sint >= 1.0)) sint = 1.0;
+    if (sint > 2147483647.0) bad = 1;
+    const int si = bad ? 1 : (int)sint;
+    for (int i = 0; i < r; ++i) {
+      sc.tc[i] = a.t[i] / si;
+      sc.cA[i] = a.alpha[i] / si;
+      sc.cD[i] = -(xi * a.t[i]) / si;
+      sc.cV[i] = exp(xi * a.t[i] / si) / si;
+    }
+    sc.xi = xi;
+    sc.s_int = si;
+    sc.bad = bad;
+  }
+  __syncthreads();
+  if (sc.bad) {
+    if (threadIdx.x == 0) set_status(ctl, PHIC_INVALID_ARG);
+    return;
+  }
+  if (a.fault && blockIdx.x == 0 && gridDim.x > 1) return;  // test hook: never arrive at the barrier
+
+  const T* __restrict__ vals = static_cast<const T*>(a.vals);
+  const T* __restrict__ Vin = static_cast<const T*>(a.Vin);
+  T* __restrict__ S = static_cast<T*>(a.S);
+  const ItemLoop it(n, L.Lp2);
+  const int lmask = L.Lp2 - 1;
+  const long long stride = (long long)gridDim.x * kBlock;
+  const int c0 = (threadIdx.x & lmask) * CW;
+
+  T kV[CW];
+  int kI[CW];
+  bool kLive[CW], kUp[CW];
+  const T* kSrc[CW];
+#pragma unroll
+  for (int j = 0; j < CW; ++j) {
+    const int c = c0 + j;
+    kLive[j] = c < L.w;
+    const int b = kLive[j] ? c / r : 0, i = kLive[j] ? c - b * r : 0;
+    kI[j] = i;
+    kV[j] = (T)sc.cV[i];
+    kUp[j] = kLive[j] && b >= 2;
+    // column block b of V holds v0 (b = 0) or v_{p+1-b} (b >= 1): [v0, vp, ..., v1]
+    kSrc[j] = !kLive[j] ? nullptr
+              : (b == 0) ? (a.no_v0 ? nullptr : Vin)
+                         : Vin + (size_t)(p + 1 - b - a.no_v0) * n;
+  }
+
+  // ---- k = 1: S = D = V -----------------------------------------------------------------------------
+  int bad = 0;
+  {
+    T* V1 = static_cast<T*>(a.Vt[1]);
+    T* D1 = static_cast<T*>(a.Dt[1]);
+    unsigned long long mx = 0;
+    for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
+      const long long item = base + threadIdx.x;
+      const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
+      const bool act = row < n && lane < L.L;
+      T part = T(0);
+      if (act) {
+        if (lane == 0) {  // CSR structure check: monotone rowptr inside [0, nnz]
+          const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
+          if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) bad = 1;
+        }
+        T x[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+          x[j] = kSrc[j] ? kSrc[j][row] * kV[j] : T(0);
+          part += tabs(x[j]);
+        }
+        const size_t o = (size_t)row * L.ws + c0;
+        VecIO<T, CW>::st(V1 + o, x);
+        VecIO<T, CW>::st(D1 + o, x);
+        VecIO<T, CW>::st(S + o, x);
+      }
+      const T rs = group_sum(part, L.Lp2);
+      if (act && lane == 0) umax(mx, (double)rs);
+    }
+    const unsigned long long m0 = block_max_u64(mx);
+    const int anybad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+      slot_max(ctl, 0, 0, m0);
+      if (anybad) set_status(ctl, PHIC_INVALID_ARG);
+    }
+  }
+  if (!grid_sync(ctl, a.spin_ns)) return;
+
+  // Loop state, meaningful in thread 0 only.
+  int phase = 0, k = 1, status = PHIC_OK;
+  double c1 = INFINITY, c2 = 0.0, nS = 0.0;
+  auto decide = [&]() {  // thread 0: evaluate  while c1 + c2 > tol ||S||  and prepare term k+1
+    int go = 0;
+    if (status == PHIC_OK && (!isfinite(c2) || !isfinite(nS))) status = PHIC_NONFINITE;  // NaN ends the test silently
+    if (status == PHIC_OK && c1 + c2 > a.tol * nS) {
+      if (k >= a.max_terms) status = PHIC_TERM_CAP;
+      else {
+        k += 1;
+        c1 = c2;
+        go = 1;
+        for (int i = 0; i < r; ++i) {
+          tk.kd[i] = (T)(sc.cD[i] / k);
+          tk.ka[i] = (T)(sc.cA[i] / k);
+          tk.kt[i] = (T)(sc.tc[i] / k);
+        }
+      }
+    }
+    lc.go = go;
+    lc.k = k;
+    lc.status = status;
+  };
+  if (threadIdx.x == 0) {
+    status = read_status(ctl);
+    c2 = slot_get(ctl, 0, 0);
+    nS = c2;
+    decide();
+  }
+  __syncthreads();
+
+  // ---- k >= 2:  V <- V Jsh;  D <- A_1 D (I kron T/s) + V;  S <- S + D/k!  (divided by k!) ----------
+  while (lc.go) {
+    const int kk = lc.k;
+    ++phase;
+    slot_reset(ctl, phase);
+    T kD[CW], kA[CW], kT[CW];
+#pragma unroll
+    for (int j = 0; j < CW; ++j) {
+      kD[j] = tk.kd[kI[j]];
+      kA[j] = tk.ka[kI[j]];
+      kT[j] = tk.kt[kI[j]];
+    }
+    const T xi = (T)sc.xi;
+    const T* __restrict__ Vo = static_cast<const T*>(a.Vt[(kk - 1) & 1]);
+    T* __restrict__ Vn = static_cast<T*>(a.Vt[kk & 1]);
+    const T* __restrict__ Do = static_cast<const T*>(a.Dt[(kk - 1) & 1]);
+    T* __restrict__ Dn = static_cast<T*>(a.Dt[kk & 1]);
+    unsigned long long mD = 0, mS = 0;
+    for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
+      const long long item = base + threadIdx.x;
+      const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
+      const bool act = row < n && lane < L.L;
+      T pD = T(0), pS = T(0);
+      if (act) {
+        const size_t o = (size_t)row * L.ws + c0;
+        T acc[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) acc[j] = T(0);
+        spmm_row<T, CW>(a.rowptr, a.colidx, vals, Do, L.ws, c0, row, n, acc, bad);
+        T own[CW], vo[CW], sv[CW], vn[CW], dn[CW];
+        VecIO<T, CW>::ld(Do + o, own);
+        VecIO<T, CW>::ld(Vo + o, vo);
+        VecIO<T, CW>::ld(S + o, sv);
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+          // block b of the new V: -xi t_i/s times block b, plus alpha_i/s times block b-1 when b >= 2
+          T v = kD[j] * vo[j];
+          if (kUp[j]) v = fma(kA[j], Vo[o + j - r], v);
+          const T d = fma(fma(-xi, own[j], acc[j]), kT[j], v);
+          const T sn = sv[j] + d;
+          vn[j] = kLive[j] ? v : T(0);
+          dn[j] = kLive[j] ? d : T(0);
+          sv[j] = kLive[j] ? sn : T(0);
+          pD += tabs(dn[j]);
+          pS += tabs(sv[j]);
+        }
+        VecIO<T, CW>::st(Vn + o, vn);
+        VecIO<T, CW>::st(Dn + o, dn);
+        VecIO<T, CW>::st(S + o, sv);
+      }
+      const T rD = group_sum(pD, L.Lp2), rS = group_sum(pS, L.Lp2);
+      if (act && lane == 0) {
+        umax(mD, (double)rD);
+        umax(mS, (double)rS);
+      }
+    }
+    const unsigned long long bD = block_max_u64(mD);
+    const unsigned long long bS = block_max_u64(mS);
+    const int anybad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+      slot_max(ctl, phase, 0, bD);
+      slot_max(ctl, phase, 1, bS);
+      if (anybad) set_status(ctl, PHIC_INVALID_ARG);
+    }
+    if (!grid_sync(ctl, a.spin_ns)) return;
+    if (threadIdx.x == 0) {
+      status = read_status(ctl);
+      c2 = slot_get(ctl, phase, 0);  // ||D_k||_inf / k!
+      nS = slot_get(ctl, phase, 1);
+      decide();
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (lc.status != PHIC_OK) set_status(ctl, lc.status);
+    a.state->s_int = sc.s_int;
+    a.state->series_terms = lc.k;
+    a.state->xi = sc.xi;
+    a.state->s = a.params->s;
+  }
+}
+
+// ===================================================================================================
+// Recovery (Algorithm 3: first-block recovery, the for loop over j, the output)
+// ===================================================================================================
+namespace {
+// Block p of S Jt^j, column i, is sum_{a=1..p} S(:, (a, i)) (j alpha_i/s)^(p-a) / (p-a)!, because
+// Jt^j = exp(j J kron Delta / s) and (J^q)[a, p] = 1 exactly when a = p - q >= 1.
+__device__ void jt_power_coeffs(RecoverScalars& rs, const SolveArgs& a, int j) {
+  const int p = a.p, r = a.r;
+  for (int idx = threadIdx.x; idx < p * r; idx += blockDim.x) {
+    const int aa = 1 + idx / r, i = idx % r;
+    const double x = (double)j * a.alpha[i] / rs.s_int;
+    double c = 1.0;
+    for (int q = 1; q <= p - aa; ++q) c = c * x / q;
+    rs.cj[aa][i] = c;
+  }
+}
+}  // namespace
+
+template <typename T, int CW>
+__global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
+  __shared__ RecoverScalars sc;
+  __shared__ LoopCtl lc;
+  Ctl* ctl = a.ctlR;
+  const int n = a.n, r = a.r, p = a.p;
+  const TileLayout L = a.F_lay;
+  const int ws_s = a.S_lay.ws;
+
+  if (threadIdx.x == 0) {
+    sc.status = read_status(a.ctlS);
+    sc.s_int = a.state->s_int;
+    sc.series_terms = a.state->series_terms;
+    sc.xi = a.state->xi;
+    if (sc.status == PHIC_OK) {
+      for (int i = 0; i < r; ++i) {
+        sc.tcF[i] = a.t[i] / sc.s_int;                 // T <- I_2 kron T/s
+        sc.mu[i] = exp(sc.xi * a.t[i] / sc.s_int);     // mu <- I_2 kron mu
+      }
+    }
+  }
+  __syncthreads();
+  long long rec_terms = 0;  // thread 0 of block 0 keeps the counts
+  int max_inner = 0;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  auto finish = [&](int st) {
+    if (leader) {
+      if (st != PHIC_OK) set_status(ctl, st);
+      const int s1 = read_status(a.ctlS);
+      const int fin = s1 != PHIC_OK ? s1 : read_status(ctl);
+      if (a.stats) {
+        a.stats->status = fin;
+        a.stats->s_int = sc.s_int;
+        a.stats->series_terms = sc.series_terms;
+        a.stats->max_inner_terms = max_inner;
+        a.stats->recovery_terms = rec_terms;
+        a.stats->spmm_count = (long long)(sc.series_terms - 1) + 1 + rec_terms;
+        a.stats->xi = sc.xi;
+        a.stats->s = a.state->s;
+      }
+    }
+  };
+  if (sc.status != PHIC_OK) {
+    finish(sc.status);
+    return;
+  }
+
+  const T* __restrict__ vals = static_cast<const T*>(a.vals);
+  const T* __restrict__ S = static_cast<const T*>(a.S);
+  const T* __restrict__ Vin = static_cast<const T*>(a.Vin);
+  T* __restrict__ E = static_cast<T*>(a.E);
+  const ItemLoop it(n, L.Lp2);
+  const int lmask = L.Lp2 - 1;
+  const long long stride = (long long)gridDim.x * kBlock;
+  const int c0 = (threadIdx.x & lmask) * CW;
+  int kI[CW];
+  bool kLive[CW], kBlkP[CW];
+  T kMu[CW], kTt[CW];
+#pragma unroll
+  for (int j = 0; j < CW; ++j) {
+    const int c = c0 + j;
+    kLive[j] = c < L.w;
+    kBlkP[j] = kLive[j] && c >= r;
+    kI[j] = !kLive[j] ? 0 : (c < r ? c : c - r);
+    kMu[j] = (T)sc.mu[kI[j]];
+    kTt[j] = (T)a.t[kI[j]];
+  }
+  int bad = 0;
+  int phase = 0;
+
+  // ---- F = S(:, [blk 0, blk p]);  F(:,1:r) <- A F(:,1:r) T + v0 1^T (unshifted A, t undivided) -----
+  {
+    T* F = static_cast<T*>(a.Ft[0]);
+    const T* v0 = a.no_v0 ? nullptr : Vin;
+    unsigned long long mx = 0;
+    for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
+      const long long item = base + threadIdx.x;
+      const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
+      const bool act = row < n && lane < L.L;
+      T part = T(0);
+      if (act) {
+        T f[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+          T v = T(0);
+          if (kLive[j] && !kBlkP[j]) {
+            const int i = kI[j];
+            T acc = T(0);
+            const int beg = __ldg(a.rowptr + row), end = __ldg(a.rowptr + row + 1);
+            for (int q = beg; q < end; ++q) {
+              const int col = __ldg(a.colidx + q);
+              if ((unsigned)col >= (unsigned)n) { bad = 1; continue; }
+              acc = fma(__ldg(vals + q), S[(size_t)col * ws_s + i], acc);
+            }
+            v = fma(acc, kTt[j], v0 ? v0[row] : T(0));
+          } else if (kBlkP[j]) {
+            v = S[(size_t)row * ws_s + p * r + kI[j]];
+          }
+          f[j] = v;
+          part += tabs(v);
+        }
+        VecIO<T, CW>::st(F + (size_t)row * L.ws + c0, f);
+      }
+      const T rs = group_sum(part, L.Lp2);
+      if (act && lane == 0) umax(mx, (double)rs);
+    }
+    const unsigned long long bm = block_max_u64(mx);
+    const int anybad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+      slot_max(ctl, phase, 0, bm);
+      if (anybad) set_status(ctl, PHIC_INVALID_ARG);
+    }
+    if (!grid_sync(ctl, a.spin_ns)) { finish(PHIC_TIMEOUT); return; }
+  }
+  // thread-0 loop state
+  int status = PHIC_OK, k = 0;
+  double cF = 0.0, c1 = 0.0, c2 = 0.0, nE = 0.0;
+  if (threadIdx.x == 0) {
+    status = read_status(ctl);
+    cF = slot_get(ctl, phase, 0);
+    lc.status = status;
+  }
+  __syncthreads();
+  int cur = 0;
+
+  // ---- for j = 1 : s-1 ------------------------------------------------------------------------------
+  for (int jstep = 1; jstep <= sc.s_int - 1 && lc.status == PHIC_OK; ++jstep) {
+    // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||
+    auto decide = [&]() {
+      int go = 0;
+      if (status == PHIC_OK && (!isfinite(c2) || !isfinite(nE))) status = PHIC_NONFINITE;
+      if (status == PHIC_OK && c1 + c2 > a.tol * nE) {
+        if (k >= a.max_terms) status = PHIC_TERM_CAP;
+        else {
+          k += 1;
+          c1 = c2;
+          go = 1;
+          for (int i = 0; i < r; ++i) sc.scale[i] = sc.tcF[i] / k;
+        }
+      }
+      lc.go = go;
+      lc.k = k;
+      lc.status = status;
+    };
+    if (threadIdx.x == 0) {
+      k = 0;
+      c1 = INFINITY;
+      c2 = cF;
+      nE = cF;
+      decide();
+    }
+    __syncthreads();
+    while (lc.go) {
+      const int kk = lc.k;
+      ++phase;
+      slot_reset(ctl, phase);
+      T kS[CW];
+#pragma unroll
+      for (int j = 0; j < CW; ++j) kS[j] = kLive[j] ? (T)sc.scale[kI[j]] : T(0);
+      const T xi = (T)sc.xi;
+      const T* __restrict__ Fo = static_cast<const T*>(a.Ft[cur]);
+      T* __restrict__ Fn = static_cast<T*>(a.Ft[cur ^ 1]);
+      unsigned long long mF = 0, mE = 0;
+      for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
+        const long long item = base + threadIdx.x;
+        const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
+        const bool act = row < n && lane < L.L;
+        T pF = T(0), pE = T(0);
+        if (act) {
+          const size_t o = (size_t)row * L.ws + c0;
+          T acc[CW];
+#pragma unroll
+          for (int j = 0; j < CW; ++j) acc[j] = T(0);
+          spmm_row<T, CW>(a.rowptr, a.colidx, vals, Fo, L.ws, c0, row, n, acc, bad);
+          T own[CW], e[CW], fn[CW];
+          VecIO<T, CW>::ld(Fo + o, own);
+          if (kk == 1) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j) e[j] = own[j];  // E = F at the start of the step
+          } else {
+            VecIO<T, CW>::ld(E + o, e);
+          }
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
+            // F <- A_1 F T / k;  E <- E + F
+            const T f = fma(-xi, own[j], acc[j]) * kS[j];
+            fn[j] = f;
+            e[j] += f;
+            pF += tabs(f);
+            pE += tabs(e[j]);
+          }
+          VecIO<T, CW>::st(Fn + o, fn);
+          VecIO<T, CW>::st(E + o, e);
+        }
+        const T rF = group_sum(pF, L.Lp2), rE = group_sum(pE, L.Lp2);
+        if (act && lane == 0) {
+          umax(mF, (double)rF);
+          umax(mE, (double)rE);
+        }
+      }
+      const unsigned long long bF = block_max_u64(mF);
+      const unsigned long long bE = block_max_u64(mE);
+      const int anybad = __syncthreads_or(bad);
+      if (threadIdx.x == 0) {
+        slot_max(ctl, phase, 0, bF);
+        slot_max(ctl, phase, 1, bE);
+        if (anybad) set_status(ctl, PHIC_INVALID_ARG);
+      }
+      if (!grid_sync(ctl, a.spin_ns)) { finish(PHIC_TIMEOUT); return; }
+      cur ^= 1;
+      if (threadIdx.x == 0) {
+        status = read_status(ctl);
+        c2 = slot_get(ctl, phase, 0);
+        nE = slot_get(ctl, phase, 1);
+        decide();
+      }
+      __syncthreads();
+    }
+    if (leader) {
+      rec_terms += lc.k;
+      max_inner = lc.k > max_inner ? lc.k : max_inner;
+    }
+    if (lc.status != PHIC_OK) break;
+
+    // ---- E <- E mu;  S <- S Jt;  F <- E + S(:, [blk 0, blk p]);  F(:,1:r) <- E(:,1:r) -------------
+    ++phase;
+    slot_reset(ctl, phase);
+    jt_power_coeffs(sc, a, jstep);
+    __syncthreads();
+    {
+      T* __restrict__ F = static_cast<T*>(a.Ft[cur]);
+      unsigned long long mx = 0;
+      for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
+        const long long item = base + threadIdx.x;
+        const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
+        const bool act = row < n && lane < L.L;
+        T part = T(0);
+        if (act) {
+          const size_t o = (size_t)row * L.ws + c0;
+          T e[CW];
+          VecIO<T, CW>::ld(E + o, e);
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
+            T v = e[j] * kMu[j];
+            if (kBlkP[j]) {
+              const int i = kI[j];
+              const T* srow = S + (size_t)row * ws_s;
+              for (int aa = 1; aa <= p; ++aa) v = fma(srow[aa * r + i], (T)sc.cj[aa][i], v);
+            }
+            e[j] = kLive[j] ? v : T(0);
+            part += tabs(e[j]);
+          }
+          VecIO<T, CW>::st(F + o, e);
+        }
+        const T rs = group_sum(part, L.Lp2);
+        if (act && lane == 0) umax(mx, (double)rs);
+      }
+      const unsigned long long bm = block_max_u64(mx);
+      if (threadIdx.x == 0) slot_max(ctl, phase, 0, bm);
+      if (!grid_sync(ctl, a.spin_ns)) { finish(PHIC_TIMEOUT); return; }
+      if (threadIdx.x == 0) {
+        cF = slot_get(ctl, phase, 0);
+        status = read_status(ctl);
+        lc.status = status;
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- w_i = F(:, i) + alpha_i F(:, r+i)   (p = 0: w_i = F(:, i) = exp(t_i A) v0) -------------------
+  if (lc.status == PHIC_OK) {
+    const T* __restrict__ F = static_cast<const T*>(a.Ft[cur]);
+    T* __restrict__ W = static_cast<T*>(a.W);
+    const long long total = (long long)n * r;
+    for (long long idx = (long long)blockIdx.x * kBlock + threadIdx.x; idx < total; idx += stride) {
+      const int i = (int)(idx / n), row = (int)(idx - (long long)i * n);
+      const T* frow = F + (size_t)row * L.ws;
+      W[idx] = (p == 0) ? frow[i] : fma((T)a.alpha[i], frow[r + i], frow[i]);
+    }
+  }
+  finish(lc.status);
+}
+
+// ---------------------------------------------------------------------------------------------------
+namespace {
+
+
+template <typename K>
+cudaError_t coop_launch(K kernel, long long items, int max_per_sm, const SolveArgs& a, cudaStream_t st,
+                        int* grid_out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  if (per_sm > max_per_sm) per_sm = max_per_sm;
+  long long need = (items + kBlock - 1) / kBlock;
+  long long grid = (long long)sms * per_sm;
+  if (need < grid) grid = need < 1 ? 1 : need;
+  if (grid_out) *grid_out = (int)grid;
+  void* args[] = {const_cast<SolveArgs*>(&a)};
+  count_launch();
+  return cudaLaunchCooperativeKernel((const void*)kernel, dim3((unsigned)grid), dim3(kBlock), args, 0, st);
+}
+
+template <typename T>
+cudaError_t dispatch_series(const SolveArgs& a, cudaStream_t st, int* g) {
+  const long long items = (long long)a.n * a.S_lay.Lp2;
+  const int bps = blocks_per_sm(sizeof(T));
+  switch (a.S_lay.cw) {
+    case 1: return coop_launch(series_kernel<T, 1>, items, bps, a, st, g);
+    case 2: return coop_launch(series_kernel<T, 2>, items, bps, a, st, g);
+    default: return coop_launch(series_kernel<T, 4>, items, bps, a, st, g);
+  }
+}
+template <typename T>
+cudaError_t dispatch_recover(const SolveArgs& a, cudaStream_t st, int* g) {
+  const long long items = (long long)a.n * a.F_lay.Lp2;
+  const int bps = blocks_per_sm(sizeof(T));
+  switch (a.F_lay.cw) {
+    case 1: return coop_launch(recover_kernel<T, 1>, items, bps, a, st, g);
+    case 2: return coop_launch(recover_kernel<T, 2>, items, bps, a, st, g);
+    default: return coop_launch(recover_kernel<T, 4>, items, bps, a, st, g);
+  }
+}
+}  // namespace
+
+cudaError_t launch_series(const SolveArgs& a, int prec, cudaStream_t st, int* grid_out) {
+  return prec == PHIC_F32 ? dispatch_series<float>(a, st, grid_out) : dispatch_series<double>(a, st, grid_out);
+}
+cudaError_t launch_recover(const SolveArgs& a, int prec, cudaStream_t st, int* grid_out) {
+  return prec == PHIC_F32 ? dispatch_recover<float>(a, st, grid_out) : dispatch_recover<double>(a, st, grid_out);
+}
+
+TileLayout pick_layout(int w) {
+  TileLayout t;
+  t.w = w;
+  if (w % 4 == 0 && w / 4 <= 32) {
+    t.cw = 4;
+    t.ws = w;
+  } else if (w % 2 == 0 && w / 2 <= 32) {
+    t.cw = 2;
+    t.ws = w;
+  } else if (w <= 32) {
+    t.cw = 1;
+    t.ws = w;
+  } else {
+    t.cw = 4;
+    t.ws = (w + 3) / 4 * 4;
+  }
+  t.L = t.ws / t.cw;
+  t.Lp2 = 1;
+  while (t.Lp2 < t.L) t.Lp2 <<= 1;
+  return t;
+}
+
+}  // namespace phic
