@@ -155,6 +155,30 @@ phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, c
                        double tol, const phic_params* params_dev, uint32_t flags, int32_t max_terms, void* W, void* ws,
                        size_t ws_bytes, phic_stats* stats_dev, int32_t prec, phic_stream_t stream);
 
+/* Size of the static scratch array used by phic_solve_noalloc (32 MiB per device). */
+#define PHIC_NOALLOC_MAX_BYTES (32u << 20)
+
+/* phic_solve without a caller-supplied workspace (the paper has no counterpart: this is an interface for
+ * callers that cannot allocate device memory).  Some callers may not call cudaMalloc at all: a plug-in
+ * running inside a host application that owns every device allocation, a latency-critical loop that
+ * cannot afford cudaMalloc's device-wide synchronisation, or a system allowed to allocate only at
+ * start-up.  This entry point takes the same arguments as phic_solve minus ws / ws_bytes and keeps its
+ * scratch in a file-scope static device array of PHIC_NOALLOC_MAX_BYTES that every GPU loading the
+ * library holds until the process exits.  It allocates nothing itself.
+ *   - Size limit: when phic_solve_workspace_size(n, p, r, prec) exceeds PHIC_NOALLOC_MAX_BYTES the call
+ *     returns PHIC_WORKSPACE_TOO_SMALL and enqueues nothing (e.g. FP64, p = 3, r = 2 fits up to about
+ *     80,000 rows).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *     device current and caches it; make that first call before any stream capture.
+ *   - Every call shares the one array, which keeps the previous call's contents (the call clears the
+ *     parts that must start at zero).  Calls whose work overlaps on the GPU -- on different streams, or
+ *     from different host threads -- race on the array and give undefined results: serialise them.
+ *   - flags may be 0 or PHIC_NO_V0; A, V, t, alpha, params_dev, W, stats_dev, prec and stream are as in
+ *     phic_solve. */
+phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t r, const void* V, const double* t,
+                               const double* alpha, double tol, const phic_params* params_dev, uint32_t flags,
+                               int32_t max_terms, void* W, phic_stats* stats_dev, int32_t prec, phic_stream_t stream);
+
 /* Bound on one grid-barrier wait of phic_solve in milliseconds (default 2000).  Applies to later calls. */
 void phic_set_spin_limit_ms(double ms);
 

@@ -16,6 +16,7 @@ PHIC_F64, PHIC_F32 = 0, 1
 PHIC_NO_V0 = 1
 PHIC_PHASE_SERIES, PHIC_PHASE_RECOVER = 0x10, 0x20
 PHIC_MAX_R, PHIC_MAX_P, PHIC_MAX_WIDTH = 16, 15, 128
+PHIC_NOALLOC_MAX_BYTES = 32 << 20
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "TERM_CAP", 4: "TIMEOUT", 5: "CUDA_ERROR",
                 6: "WORKSPACE_TOO_SMALL"}
@@ -65,6 +66,9 @@ SIGNATURES = [
     ("phic_solve", ctypes.c_int, [ctypes.POINTER(phic_csr), ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
                                   ctypes.c_double, _P, ctypes.c_uint32, ctypes.c_int32, _P, _P, ctypes.c_size_t, _P,
                                   ctypes.c_int32, _P]),
+    ("phic_solve_noalloc", ctypes.c_int, [ctypes.POINTER(phic_csr), ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
+                                          ctypes.c_double, _P, ctypes.c_uint32, ctypes.c_int32, _P, _P,
+                                          ctypes.c_int32, _P]),
     ("phic_set_spin_limit_ms", None, [ctypes.c_double]),
     ("phic_set_blocks_per_sm", None, [ctypes.c_int32]),
     ("phic_set_test_fault", None, [ctypes.c_int32]),

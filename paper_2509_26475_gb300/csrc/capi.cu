@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -232,3 +233,90 @@ uint64_t phic_launch_count(void) { return g_launches.load(); }
 int32_t phic_version(void) { return 100; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------------
+// phic_solve_noalloc: the solve kernels with their scratch in a static device array instead of a
+// caller-supplied workspace, for callers that cannot allocate device memory.
+// ---------------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PHIC_NOALLOC_MAX_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 128;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.  In host code
+// the array's name is only a host-side stand-in, so the kernels must be given this address.
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t r, const void* V, const double* t,
+                                          const double* alpha, double tol, const phic_params* params_dev,
+                                          uint32_t flags, int32_t max_terms, void* W, phic_stats* stats_dev,
+                                          int32_t prec, phic_stream_t stream) {
+  if (!csr_ok(A) || A->prec != prec || !V || !W || !t || !alpha || !params_dev) return PHIC_INVALID_ARG;
+  if (p < 0 || p > PHIC_MAX_P || r < 1 || r > PHIC_MAX_R || (p + 1) * r > PHIC_MAX_WIDTH) return PHIC_INVALID_ARG;
+  if (!(tol > 0.0) || !std::isfinite(tol)) return PHIC_INVALID_ARG;
+  if ((flags & ~PHIC_NO_V0) != 0 || ((flags & PHIC_NO_V0) && p == 0)) return PHIC_INVALID_ARG;
+  for (int i = 0; i < r; ++i)
+    if (!std::isfinite(t[i]) || !std::isfinite(alpha[i])) return PHIC_INVALID_ARG;
+  const SolveLayout L = solve_layout(A->n, p, r, prec);
+  if (L.total > (size_t)PHIC_NOALLOC_MAX_BYTES) return PHIC_WORKSPACE_TOO_SMALL;
+  void* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) return PHIC_CUDA_ERROR;
+  char* base = static_cast<char*>(scratch);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // control blocks and loop state must start at zero; the tiles are written before they are read
+  if (cudaMemsetAsync(base, 0, L.Vt[0], st) != cudaSuccess) return PHIC_CUDA_ERROR;
+  SolveArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = (int)A->n;
+  a.nnz = (int)A->nnz;
+  a.rowptr = A->rowptr;
+  a.colidx = A->colidx;
+  a.vals = A->values;
+  a.Vin = V;
+  a.W = W;
+  a.p = p;
+  a.r = r;
+  a.no_v0 = (flags & PHIC_NO_V0) ? 1 : 0;
+  a.S_lay = L.sl;
+  a.F_lay = L.fl;
+  for (int i = 0; i < r; ++i) {
+    a.t[i] = t[i];
+    a.alpha[i] = alpha[i];
+  }
+  a.tol = tol;
+  a.max_terms = max_terms > 0 ? max_terms : 610;
+  a.params = params_dev;
+  for (int q = 0; q < 2; ++q) {
+    a.Vt[q] = base + L.Vt[q];
+    a.Dt[q] = base + L.Dt[q];
+    a.Ft[q] = base + L.Ft[q];
+  }
+  a.S = base + L.S;
+  a.E = base + L.E;
+  a.ctlS = reinterpret_cast<Ctl*>(base + L.ctlS);
+  a.ctlR = reinterpret_cast<Ctl*>(base + L.ctlR);
+  a.state = reinterpret_cast<SolveState*>(base + L.state);
+  a.stats = stats_dev;
+  a.spin_ns = (unsigned long long)g_spin_ns.load();
+  a.fault = 0;
+  if (launch_series(a, prec, st, nullptr) != cudaSuccess) return PHIC_CUDA_ERROR;
+  if (launch_recover(a, prec, st, nullptr) != cudaSuccess) return PHIC_CUDA_ERROR;
+  return PHIC_OK;
+}
