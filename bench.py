@@ -168,12 +168,12 @@ class ClockSampler:
 def recover_kernel_work(n, nnz, wf, p, r, terms, outer_steps):
     """Algorithmic FP64 operations and bytes of one recovery-kernel launch.
 
-    Per Taylor term (n x wf block, wf = 2r): the shifted product (A - xi I) F takes nnz + n
-    multiply-adds per column, the column scale t_i/(s k) n, E <- E + F n, and the two infinity-norm row
-    sums 2n operations per column: (nnz + 5n) wf.  Per recovery step the refresh E mu + S Jt costs
-    (2 + p/2) n wf.  Bytes per term: CSR values and indices (12 nnz + 4(n+1)) plus reading F, reading
-    and writing E and writing the next F (4 n wf 8)."""
-    ops = terms * (nnz + 5 * n) * wf + outer_steps * (2 + p / 2.0) * n * wf
+    Per Taylor term (n x wf block, wf = 2r): the product with A_1 = A - xi I (formed once per solve, as
+    Algorithm 3 writes it) takes nnz multiply-adds per column, the column scale t_i/(s k) n,
+    E <- E + F n, and the two infinity-norm row sums 2n operations per column: (nnz + 4n) wf.  Per
+    recovery step the refresh E mu + S Jt costs (2 + p/2) n wf.  Bytes per term: CSR values and indices
+    (12 nnz + 4(n+1)) plus reading F, reading and writing E and writing the next F (4 n wf 8)."""
+    ops = terms * (nnz + 4 * n) * wf + outer_steps * (2 + p / 2.0) * n * wf
     bytes_ = terms * (12 * nnz + 4 * (n + 1) + 4 * n * wf * 8)
     return ops, bytes_
 
@@ -206,7 +206,7 @@ def main():
     stats = [api.new_stats(dev) for _ in HS]
     W = [torch.empty((R, n), dtype=torch.float64, device=dev) for _ in HS]
     ws_sel = torch.empty(api.select_workspace_bytes(n), dtype=torch.uint8, device=dev)
-    ws_sol = torch.empty(api.solve_workspace_bytes(n, P, R, capi.PHIC_F64), dtype=torch.uint8, device=dev)
+    ws_sol = torch.empty(api.solve_workspace_bytes(n, nnz, P, R, capi.PHIC_F64), dtype=torch.uint8, device=dev)
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)

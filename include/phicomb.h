@@ -134,8 +134,10 @@ phic_status phic_select_params(const phic_csr* A, const phic_select_opts* opts, 
 /* Writes user-chosen xi and s into params_dev (device) on `stream`, for callers that skip Algorithm 1. */
 phic_status phic_params_set(phic_params* params_dev, double xi, double s, phic_stream_t stream);
 
-/* Workspace bytes needed by phic_solve for n rows, p, r and the storage precision. */
-phic_status phic_solve_workspace_size(int64_t n, int32_t p, int32_t r, int32_t prec, size_t* bytes);
+/* Workspace bytes needed by phic_solve for n rows, nnz stored entries, p, r and the storage precision:
+ * a copy of the values holding A_1 = A - xi I, the block tiles V, D (two each), S, F (two), E, and
+ * control blocks. */
+phic_status phic_solve_workspace_size(int64_t n, int64_t nnz, int32_t p, int32_t r, int32_t prec, size_t* bytes);
 
 /* Algorithm 3 (Section 4): w_i = sum_j alpha_i^j phi_j(t_i A) v_j for i = 1..r.
  *   A       CSR operator; A->prec must equal `prec`.
@@ -165,9 +167,9 @@ phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, c
  * start-up.  This entry point takes the same arguments as phic_solve minus ws / ws_bytes and keeps its
  * scratch in a file-scope static device array of PHIC_NOALLOC_MAX_BYTES that every GPU loading the
  * library holds until the process exits.  It allocates nothing itself.
- *   - Size limit: when phic_solve_workspace_size(n, p, r, prec) exceeds PHIC_NOALLOC_MAX_BYTES the call
- *     returns PHIC_WORKSPACE_TOO_SMALL and enqueues nothing (e.g. FP64, p = 3, r = 2 fits up to about
- *     80,000 rows).
+ *   - Size limit: when phic_solve_workspace_size(n, nnz, p, r, prec) exceeds PHIC_NOALLOC_MAX_BYTES the
+ *     call returns PHIC_WORKSPACE_TOO_SMALL and enqueues nothing (e.g. FP64, p = 3, r = 2 and a 7-point
+ *     stencil fit up to about 70,000 rows).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
  *     device current and caches it; make that first call before any stream capture.
  *   - Every call shares the one array, which keeps the previous call's contents (the call clears the

@@ -101,9 +101,9 @@ def select_workspace_bytes(n: int, m: int = 61) -> int:
     return int(out.value)
 
 
-def solve_workspace_bytes(n: int, p: int, r: int, prec: int) -> int:
+def solve_workspace_bytes(n: int, nnz: int, p: int, r: int, prec: int) -> int:
     out = ctypes.c_size_t(0)
-    capi.check(capi.load().phic_solve_workspace_size(int(n), int(p), int(r), int(prec), ctypes.byref(out)),
+    capi.check(capi.load().phic_solve_workspace_size(int(n), int(nnz), int(p), int(r), int(prec), ctypes.byref(out)),
                "phic_solve_workspace_size")
     return int(out.value)
 
@@ -186,7 +186,7 @@ def solve(A: DeviceCSR, V: torch.Tensor, t, alpha, tol: float, params: torch.Ten
     if W.shape != (r, A.n) or W.dtype != dt or not W.is_contiguous():
         raise ValueError("out has the wrong shape or dtype")
     stats = stats if stats is not None else new_stats(dev)
-    nbytes = solve_workspace_bytes(A.n, p, r, prec)
+    nbytes = solve_workspace_bytes(A.n, A.nnz, p, r, prec)
     ws = workspace if workspace is not None else workspaces.get(("solve", prec), nbytes, dev)
     c = A.struct()
     st = lib.phic_solve(ctypes.byref(c), int(p), int(r), V.data_ptr(), t.ctypes.data, alpha.ctypes.data, float(tol),

@@ -44,10 +44,10 @@ SelectLayout select_layout(int64_t n, int m) {
 }
 
 struct SolveLayout {
-  size_t ctlS, ctlR, state, Vt[2], Dt[2], S, Ft[2], E, total;
+  size_t ctlS, ctlR, state, A1, Vt[2], Dt[2], S, Ft[2], E, total;
   TileLayout sl, fl;
 };
-SolveLayout solve_layout(int64_t n, int p, int r, int prec) {
+SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec) {
   SolveLayout L;
   const size_t es = prec == PHIC_F32 ? 4 : 8;
   L.sl = pick_layout((p + 1) * r);
@@ -58,12 +58,15 @@ SolveLayout solve_layout(int64_t n, int p, int r, int prec) {
   L.ctlS = off; off += align_up(sizeof(Ctl));
   L.ctlR = off; off += align_up(sizeof(Ctl));
   L.state = off; off += align_up(sizeof(SolveState));
+  const size_t head = off;  // control blocks and state: zeroed before each solve
+  L.A1 = off; off += align_up((size_t)(nnz > 0 ? nnz : 1) * es);
   for (int q = 0; q < 2; ++q) { L.Vt[q] = off; off += tileS; }
   for (int q = 0; q < 2; ++q) { L.Dt[q] = off; off += tileS; }
   L.S = off; off += tileS;
   for (int q = 0; q < 2; ++q) { L.Ft[q] = off; off += tileF; }
   L.E = off; off += tileF;
   L.total = off;
+  (void)head;
   return L;
 }
 }  // namespace
@@ -139,11 +142,11 @@ phic_status phic_params_set(phic_params* params_dev, double xi, double s, phic_s
              ? PHIC_OK : PHIC_CUDA_ERROR;
 }
 
-phic_status phic_solve_workspace_size(int64_t n, int32_t p, int32_t r, int32_t prec, size_t* bytes) {
-  if (!bytes || n < 1 || n >= (int64_t)INT32_MAX || p < 0 || p > PHIC_MAX_P || r < 1 || r > PHIC_MAX_R ||
-      (p + 1) * r > PHIC_MAX_WIDTH || (prec != PHIC_F64 && prec != PHIC_F32))
+phic_status phic_solve_workspace_size(int64_t n, int64_t nnz, int32_t p, int32_t r, int32_t prec, size_t* bytes) {
+  if (!bytes || n < 1 || n >= (int64_t)INT32_MAX || nnz < 0 || nnz >= (int64_t)INT32_MAX || p < 0 ||
+      p > PHIC_MAX_P || r < 1 || r > PHIC_MAX_R || (p + 1) * r > PHIC_MAX_WIDTH || (prec != PHIC_F64 && prec != PHIC_F32))
     return PHIC_INVALID_ARG;
-  *bytes = solve_layout(n, p, r, prec).total;
+  *bytes = solve_layout(n, nnz, p, r, prec).total;
   return PHIC_OK;
 }
 
@@ -163,11 +166,11 @@ phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, c
   }
   for (int i = 0; i < r; ++i)
     if (!std::isfinite(t[i]) || !std::isfinite(alpha[i])) return PHIC_INVALID_ARG;
-  const SolveLayout L = solve_layout(A->n, p, r, prec);
+  const SolveLayout L = solve_layout(A->n, A->nnz, p, r, prec);
   if (ws_bytes < L.total) return PHIC_WORKSPACE_TOO_SMALL;
   char* base = static_cast<char*>(ws);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (run_series && cudaMemsetAsync(base, 0, L.Vt[0], st) != cudaSuccess) return PHIC_CUDA_ERROR;  // control + state
+  if (run_series && cudaMemsetAsync(base, 0, L.A1, st) != cudaSuccess) return PHIC_CUDA_ERROR;  // control + state
   SolveArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = (int)A->n;
@@ -175,6 +178,7 @@ phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, c
   a.rowptr = A->rowptr;
   a.colidx = A->colidx;
   a.vals = A->values;
+  a.A1 = base + L.A1;
   a.Vin = V;
   a.W = W;
   a.p = p;
@@ -274,14 +278,14 @@ extern "C" phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t 
   if ((flags & ~PHIC_NO_V0) != 0 || ((flags & PHIC_NO_V0) && p == 0)) return PHIC_INVALID_ARG;
   for (int i = 0; i < r; ++i)
     if (!std::isfinite(t[i]) || !std::isfinite(alpha[i])) return PHIC_INVALID_ARG;
-  const SolveLayout L = solve_layout(A->n, p, r, prec);
+  const SolveLayout L = solve_layout(A->n, A->nnz, p, r, prec);
   if (L.total > (size_t)PHIC_NOALLOC_MAX_BYTES) return PHIC_WORKSPACE_TOO_SMALL;
   void* scratch = nullptr;
   if (noalloc_scratch(&scratch) != cudaSuccess) return PHIC_CUDA_ERROR;
   char* base = static_cast<char*>(scratch);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // control blocks and loop state must start at zero; the tiles are written before they are read
-  if (cudaMemsetAsync(base, 0, L.Vt[0], st) != cudaSuccess) return PHIC_CUDA_ERROR;
+  if (cudaMemsetAsync(base, 0, L.A1, st) != cudaSuccess) return PHIC_CUDA_ERROR;
   SolveArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = (int)A->n;
@@ -289,6 +293,7 @@ extern "C" phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t 
   a.rowptr = A->rowptr;
   a.colidx = A->colidx;
   a.vals = A->values;
+  a.A1 = base + L.A1;
   a.Vin = V;
   a.W = W;
   a.p = p;

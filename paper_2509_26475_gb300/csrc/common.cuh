@@ -13,12 +13,11 @@ constexpr int kBlock = 256;  // threads per block of every persistent kernel
 
 // Control block at the head of each persistent kernel's workspace region; zeroed before launch.
 struct __align__(256) Ctl {
-  unsigned bar_count;  // arrivals at the current grid barrier
-  unsigned bar_gen;    // completed grid barriers
-  int status;          // first phic_status != OK seen by any block
-  int fault;           // test hook: block 0 leaves before its first barrier when set
-  unsigned long long slot[4][4];  // max-reduction slots (bit patterns of non-negative doubles), by phase % 4
-  double pad[12];
+  unsigned long long bar;  // grid-barrier arrivals since launch (monotone: epoch e completes at e * gridDim.x)
+  int status;              // first phic_status != OK seen by any block
+  int fault;               // unused padding kept for layout stability
+  unsigned long long slot[4][4];  // max-reduction slots (bit patterns of non-negative values), by phase % 4
+  double pad[13];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte line");
 
@@ -32,43 +31,59 @@ __device__ __forceinline__ void set_status(Ctl* c, int st) { atomicCAS(&c->statu
 
 __device__ __forceinline__ int read_status(const Ctl* c) { return *(volatile const int*)&c->status; }
 
-// Grid-wide barrier of a cooperative launch.  Every thread of every block calls it.  A wait longer
-// than spin_ns sets PHIC_TIMEOUT and returns false in every thread of the block that gave up; the
-// caller then leaves the kernel, so no block ever waits without bound.  Writes made before the
-// barrier by any thread of the grid are visible after it (block barrier + gpu-scope fences).
-__device__ __forceinline__ bool grid_sync(Ctl* c, unsigned long long spin_ns) {
-  __shared__ int s_ok;
+__device__ __forceinline__ void bar_arrive(unsigned long long* p) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
+}
+__device__ __forceinline__ unsigned long long bar_load(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch with leader work on both sides.  Every thread of every
+// block calls it; `epoch` (kept by thread 0 of each block) counts the barriers this block has passed.
+// Thread 0 runs pre() after its block's threads have arrived (their writes are visible to it) and before
+// it signals arrival with a release reduction on the monotone counter; it then polls the counter with
+// acquire loads until every block has arrived (epoch * gridDim.x arrivals), runs post() (reads the grid
+// results, decides, writes shared memory) and releases the block.  The release/acquire pair orders
+// every write made before the barrier by any thread of the grid before every read after it.  A wait
+// longer than spin_ns sets PHIC_TIMEOUT and returns false in every thread of the block that gave up;
+// the caller then leaves the kernel, so no block ever waits without bound.
+template <typename Pre, typename Post>
+__device__ __forceinline__ bool grid_sync_lead(Ctl* c, unsigned long long& epoch, unsigned long long spin_ns,
+                                               Pre&& pre, Post&& post) {
+  __shared__ int s_ok2;
   __syncthreads();
   if (threadIdx.x == 0) {
+    pre();
     int ok = 1;
+    epoch += 1;
     if (gridDim.x > 1) {
-      volatile unsigned* gen = &c->bar_gen;
-      const unsigned g = *gen;
-      __threadfence();
-      const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(&c->bar_count, 0u);
-        __threadfence();
-        atomicAdd(&c->bar_gen, 1u);
-      } else {
+      const unsigned long long target = epoch * gridDim.x;
+      bar_arrive(&c->bar);
+      if (bar_load(&c->bar) < target) {
         const unsigned long long t0 = global_ns();
         unsigned spins = 0;
-        while (*gen == g) {
-          if ((++spins & 63u) == 0 && global_ns() - t0 > spin_ns) {
+        while (bar_load(&c->bar) < target) {
+          if ((++spins & 31u) == 0 && global_ns() - t0 > spin_ns) {
             ok = 0;
             set_status(c, PHIC_TIMEOUT);
             break;
           }
         }
       }
-      __threadfence();
     } else {
       __threadfence();
     }
-    s_ok = ok;
+    if (ok) post();
+    s_ok2 = ok;
   }
   __syncthreads();
-  return s_ok != 0;
+  return s_ok2 != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(Ctl* c, unsigned long long& epoch, unsigned long long spin_ns) {
+  return grid_sync_lead(c, epoch, spin_ns, [] {}, [] {});
 }
 
 // ---- max over the grid of non-negative doubles, carried as their bit patterns --------------------

@@ -31,6 +31,7 @@ struct SolveArgs {
   const int* rowptr;
   const int* colidx;
   const void* vals;
+  void* A1;  // workspace copy of the values with xi subtracted from the stored diagonal (A_1 = A - xi I)
   const void* Vin;
   void* W;
   int p, r, no_v0;

@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
   const long long first = (long long)blockIdx.x * kBlock + threadIdx.x;
   int pc = 0;  // pass counter (parity of the partial buffer)
   int bad = 0;
+  unsigned long long epoch = 0;  // grid barriers passed (thread 0)
 
   if (threadIdx.x == 0) {
     double lmax = -INFINITY;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
     const Ssq blk = block_ssq(acc);
     put_partial(part, pc & 1, blk);
     if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(ctl, PHIC_INVALID_ARG);
-    if (!grid_sync(ctl, a.spin_ns)) return;
+    if (!grid_sync(ctl, epoch, a.spin_ns)) return;
     const Ssq tot = gather_partials(part, pc & 1);
     ++pc;
     if (threadIdx.x == 0) {
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
     }
     const Ssq blk = block_ssq(acc);
     put_partial(part, pc & 1, blk);
-    if (!grid_sync(ctl, a.spin_ns)) return;
+    if (!grid_sync(ctl, epoch, a.spin_ns)) return;
     const Ssq tot = gather_partials(part, pc & 1);
     ++pc;
     if (threadIdx.x == 0) {
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
     const Ssq blk = block_ssq(acc);
     put_partial(part, pc & 1, blk);
     if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(ctl, PHIC_INVALID_ARG);
-    if (!grid_sync(ctl, a.spin_ns)) return;
+    if (!grid_sync(ctl, epoch, a.spin_ns)) return;
     const Ssq tot = gather_partials(part, pc & 1);
     ++pc;
     if (threadIdx.x == 0) {
@@ -293,14 +294,14 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
   __syncthreads();
   for (long long row = first; row < n; row += stride)
     for (int j = 1; j <= r; ++j) a.Vb[(size_t)j * n + row] *= sh.coef[j];
-  if (!grid_sync(ctl, a.spin_ns)) return;
+  if (!grid_sync(ctl, epoch, a.spin_ns)) return;
   // ---- extend: V_k = A V_{k-1} / s0, k = r+1..m -------------------------------------------------------
   for (int k = r + 1; k <= m; ++k) {
     const double* __restrict__ Vp = a.Vb + (size_t)(k - 1) * n;
     double* __restrict__ Vk = a.Vb + (size_t)k * n;
     const double inv_s0 = sh.inv_s0;
     for (long long row = first; row < n; row += stride) Vk[row] = spmv_row<VT>(a, vals, Vp, (int)row, bad) * inv_s0;
-    if (!grid_sync(ctl, a.spin_ns)) return;
+    if (!grid_sync(ctl, epoch, a.spin_ns)) return;
   }
   // ---- Brent on f(xi) ---------------------------------------------------------------------------------
   if (threadIdx.x == 0) {
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
     }
     const Ssq blk = block_ssq(acc);
     put_partial(part, pc & 1, blk);
-    if (!grid_sync(ctl, a.spin_ns)) return;
+    if (!grid_sync(ctl, epoch, a.spin_ns)) return;
     const Ssq tot = gather_partials(part, pc & 1);
     ++pc;
     if (threadIdx.x == 0) {

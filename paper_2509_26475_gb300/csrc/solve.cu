@@ -2,76 +2,193 @@
 // w_i = sum_j alpha_i^j phi_j(t_i A) v_j, i = 1..r.
 //
 // Two persistent cooperative kernels share one workspace:
-//   series_kernel   -- setup, then the block series S = sum_k D_k / k! of Theorem 1 (eq. rec.D with
-//                      the shift of eq. cD.shift), term by term with the truncation test (3.3).
+//   series_kernel   -- setup (A_1 = A - xi I formed once, the reordered and scaled V), then the block
+//                      series S = sum_k D_k / k! of Theorem 1 (eq. rec.D with the shift of
+//                      eq. cD.shift), term by term with the truncation test (3.3).
 //   recover_kernel  -- the first-block recovery F(:,1:r) <- A F(:,1:r) T + v0 1^T, the s-1 recovery
 //                      steps of eq. rec.F.shift (Taylor series of exp(A_1 T/s) with the same test, the
 //                      undo factor mu and the refresh from S), and the output w_i = F_i + alpha_i F_{r+i}.
 // The data-dependent loops never return to the host: every Taylor term ends at a bounded grid barrier
-// after which thread 0 of every block reads the same grid-wide norms, takes the same branch and
-// broadcasts it to its block.
+// inside which thread 0 of every block reads the same grid-wide norms, takes the same branch and
+// publishes it to its block.
 //
-// Tiles are row-major: row i of an n x w block is w consecutive values at row stride ws (see
+// Work split: block b owns the contiguous rows [b n / G, (b+1) n / G) in every pass (balanced to one
+// row).  Tiles are row-major: row i of an n x w block is w consecutive values at row stride ws (see
 // pick_layout).  Each row is processed by L lanes of CW columns; the lanes of a row are consecutive in
 // a warp, so the row sums of |x| for the infinity norm are shuffle reductions.  A thread keeps the
-// same lane in every pass (the grid stride is a multiple of the block size, itself a multiple of the
-// lane group), so its per-column constants live in registers.
+// same lane in every pass, so its per-column constants live in registers.
+//
+// On GB300 the FP64 pipe (2 FMA/clk/SM) bounds these kernels, so the per-element FP64 work is kept to
+// the products with A_1, one scale and one accumulation: the infinity norms of the terms, which only
+// decide when a Taylor loop stops, are summed in FP32 from the high words of the doubles (norm_piece).
 #include <math.h>
 
 #include "common.cuh"
 #include "kernels.h"
 
+// Tile shape of the block kernels: widest column chunk a lane takes (1, 2 or 4) and the minimum
+// resident blocks per SM requested from the register allocator.
+#ifndef PHIC_CW_MAX
+#define PHIC_CW_MAX 4
+#endif
+#ifndef PHIC_MIN_BLOCKS
+#define PHIC_MIN_BLOCKS 1
+#endif
+
 namespace phic {
 
 namespace {
 
-// Items (row, lane) of one pass; the bound is uniform across each block so that the shuffles inside
-// the body always see full warps.
-struct ItemLoop {
-  long long total;  // n * Lp2 rounded up to a multiple of the block size
-  int shift;        // log2(Lp2)
-  __device__ ItemLoop(int n, int Lp2) {
+// Contiguous rows of this block and the walk over their (row, lane) items in steps of the block size
+// (uniform within the block, so the shuffles always see full warps).
+struct BlockRows {
+  int r0, r1;
+  int shift;         // log2(Lp2)
+  long long padded;  // (r1 - r0) * Lp2 rounded up to a multiple of the block size
+  __device__ BlockRows(int n, int Lp2) {
+    r0 = (int)((long long)blockIdx.x * n / gridDim.x);
+    r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
     shift = __ffs(Lp2) - 1;
-    const long long items = (long long)n << shift;
-    total = (items + kBlock - 1) / kBlock * kBlock;
+    const long long items = (long long)(r1 - r0) << shift;
+    padded = (items + kBlock - 1) / kBlock * kBlock;
   }
 };
-
-template <typename T>
-__device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
 __device__ __forceinline__ void umax(unsigned long long& m, double v) {
   const unsigned long long u = dbits(v);
   m = u > m ? u : m;
 }
 
-// acc[j] += sum_q A(row, col_q) X(col_q, c0 + j) over the row's nonzeros; flags a bad column index
-// and skips it, so no address outside X is read.
+// Per-warp maxima of two norms and the bad-index flag; thread 0 folds them into the grid slots
+// inside the barrier.
+struct WarpParts {
+  unsigned long long a[kBlock / 32], b[kBlock / 32];
+  int bad[kBlock / 32], nonfinite[kBlock / 32];
+};
+
+__device__ __forceinline__ void warp_parts(WarpParts& wp, unsigned long long a, unsigned long long b, int bad,
+                                           int nonfinite = 0) {
+  a = warp_max_u64(a);
+  b = warp_max_u64(b);
+  const int anyb = __any_sync(0xffffffffu, bad);
+  const int anyn = __any_sync(0xffffffffu, nonfinite);
+  if ((threadIdx.x & 31) == 0) {
+    wp.a[threadIdx.x >> 5] = a;
+    wp.b[threadIdx.x >> 5] = b;
+    wp.bad[threadIdx.x >> 5] = anyb;
+    wp.nonfinite[threadIdx.x >> 5] = anyn;
+  }
+}
+
+// Slot 2 collects the non-finite flag of a pass (as 0/1).
+__device__ __forceinline__ void parts_to_slots(Ctl* c, int phase, const WarpParts& wp) {
+  unsigned long long a = 0, b = 0;
+  int bad = 0, nf = 0;
+  for (int w = 0; w < kBlock / 32; ++w) {
+    a = wp.a[w] > a ? wp.a[w] : a;
+    b = wp.b[w] > b ? wp.b[w] : b;
+    bad |= wp.bad[w];
+    nf |= wp.nonfinite[w];
+  }
+  slot_max(c, phase, 0, a);
+  slot_max(c, phase, 1, b);
+  if (nf) slot_max(c, phase, 2, 1ull);
+  if (bad) set_status(c, PHIC_INVALID_ARG);
+}
+
+// Grid-wide norm published in a slot by the float path, back to FP64 (scaled by 2^e0).
+__device__ __forceinline__ double slot_norm(const Ctl* c, int phase, int idx, int e0) {
+  const unsigned long long u = *(volatile const unsigned long long*)&c->slot[phase & 3][idx];
+  return ldexp((double)__int_as_float((int)(unsigned)u), e0);
+}
+__device__ __forceinline__ bool slot_nonfinite(const Ctl* c, int phase) {
+  return *(volatile const unsigned long long*)&c->slot[phase & 3][2] != 0ull;
+}
+__device__ __forceinline__ void fmax_bits(unsigned long long& m, float v) {
+  const unsigned long long u = (unsigned)__float_as_int(v);
+  m = u > m ? u : m;
+}
+// bias of norm_piece for the scale 2^-e0
+__device__ __forceinline__ int norm_bias(int e0) { return (896 + e0) << 20; }
+__device__ __forceinline__ int scale_exponent(double ref) {
+  return (ref > 0.0 && isfinite(ref)) ? ilogb(ref) : 0;
+}
+
+// acc[j] += sum_q M(row, col_q) X(col_q, c0 + j) over the row's nonzeros, four nonzeros at a time so
+// that their gathers are in flight together.  A column index outside [0, n) is flagged and replaced by
+// the row itself with a zero weight, so no address outside X is read and the loop has no branch on data.
+// Returns whether the row stores a diagonal entry.
 template <typename T, int CW>
-__device__ __forceinline__ void spmm_row(const int* __restrict__ rowptr, const int* __restrict__ colidx,
+__device__ __forceinline__ bool spmm_row(const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                          const T* __restrict__ vals, const T* __restrict__ X, int ws, int c0,
                                          int row, int n, T (&acc)[CW], int& bad) {
   const int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
-  for (int q = beg; q < end; ++q) {
-    const int col = __ldg(colidx + q);
-    const T av = __ldg(vals + q);
-    if ((unsigned)col >= (unsigned)n) {
-      bad = 1;
-      continue;
-    }
-    T x[CW];
-    VecIO<T, CW>::ld(X + (size_t)col * ws + c0, x);
+  bool diag = false;
+  for (int q0 = beg; q0 < end; q0 += 4) {
+    const int cnt = end - q0;
+    int col[4];
+    T av[4];
 #pragma unroll
-    for (int j = 0; j < CW; ++j) acc[j] = fma(av, x[j], acc[j]);
+    for (int u = 0; u < 4; ++u) {
+      col[u] = row;
+      av[u] = T(0);
+      if (u < cnt) {
+        const int c = __ldg(colidx + q0 + u);
+        const bool ok = (unsigned)c < (unsigned)n;
+        bad |= !ok;
+        diag |= (c == row);
+        col[u] = ok ? c : row;
+        av[u] = ok ? __ldg(vals + q0 + u) : T(0);
+      }
+    }
+    T x[4][CW];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (u < cnt) VecIO<T, CW>::ld(X + (size_t)col[u] * ws + c0, x[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (u < cnt) {
+#pragma unroll
+        for (int j = 0; j < CW; ++j) acc[j] = fma(av[u], x[u][j], acc[j]);
+      }
   }
+  return diag;
+}
+
+// |x| 2^-e0 as an FP32 value, for the infinity-norm sums that feed the truncation test.  For a double
+// the high word (sign, exponent, 20 mantissa bits) is rebiased into FP32 layout with integer
+// operations (relative truncation below 2^-20; values under 2^-126 of the scale flush to 0, values above
+// 2^128 saturate) so that the norms cost no FP64 instruction; Inf and NaN raise `nonfinite`.  bias
+// carries (896 + e0) << 20.  An FP32 element is scaled exactly.
+__device__ __forceinline__ float norm_piece(double x, int bias, float scale, int& nonfinite) {
+  (void)scale;
+  const int h = __double2hiint(x) & 0x7fffffff;
+  nonfinite |= h >= 0x7ff00000;
+  int t = h - bias;
+  t = t < 0 ? 0 : t;
+  t = t > 0x0FEFFFFF ? 0x0FEFFFFF : t;
+  return __int_as_float(t << 3);
+}
+__device__ __forceinline__ float norm_piece(float x, int bias, float scale, int& nonfinite) {
+  (void)bias;
+  nonfinite |= !isfinite(x);
+  return fabsf(x) * scale;
 }
 
 // Block-level broadcast of the loop decision made by thread 0.
 struct LoopCtl {
-  int go;            // 1: run another term
-  int k;             // index of the term to run
+  int go;       // 1: run another term
+  int k;        // index of the term to run
   int status;
+  int bias;     // norm_piece bias of the current scale 2^-e0
+  float fscale; // 2^-e0 as a float (FP32 tiles)
 };
+
+__device__ __forceinline__ void set_norm_scale(LoopCtl& lc, int e0) {
+  lc.bias = norm_bias(e0);
+  const int ef = e0 < -126 ? -126 : (e0 > 126 ? 126 : e0);
+  lc.fscale = exp2f((float)-ef);
+}
 
 // Per-term column coefficients of the series, already divided by k (see series_kernel).
 template <typename T>
@@ -84,9 +201,11 @@ struct SeriesScalars {
   int s_int, bad;
 };
 
+template <typename T>
 struct RecoverScalars {
-  double xi, tcF[PHIC_MAX_R], mu[PHIC_MAX_R], scale[PHIC_MAX_R];
-  double cj[PHIC_MAX_P + 1][PHIC_MAX_R];
+  double xi, tcF[PHIC_MAX_R], mu[PHIC_MAX_R];
+  T scale[PHIC_MAX_R];
+  T cj[PHIC_MAX_P + 1][PHIC_MAX_R];
   int s_int, series_terms, status;
 };
 
@@ -100,10 +219,11 @@ struct RecoverScalars {
 // which equals the paper's D_k / k! and V_k / k! term by term but never holds the growing X^k D_1,
 // which would overflow FP32 (and, for a large ||X||, FP64) long before the terms become small.
 template <typename T, int CW>
-__global__ void __launch_bounds__(kBlock) series_kernel(const SolveArgs a) {
+__global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const SolveArgs a) {
   __shared__ SeriesScalars sc;
   __shared__ LoopCtl lc;
   __shared__ SeriesTerm<T> tk;
+  __shared__ WarpParts wp;
   Ctl* ctl = a.ctlS;
   const int n = a.n, r = a.r, p = a.p;
   const TileLayout L = a.S_lay;
@@ -137,11 +257,11 @@ __global__ void __launch_bounds__(kBlock) series_kernel(const SolveArgs a) {
   if (a.fault && blockIdx.x == 0 && gridDim.x > 1) return;  // test hook: never arrive at the barrier
 
   const T* __restrict__ vals = static_cast<const T*>(a.vals);
+  T* __restrict__ A1 = static_cast<T*>(a.A1);
   const T* __restrict__ Vin = static_cast<const T*>(a.Vin);
   T* __restrict__ S = static_cast<T*>(a.S);
-  const ItemLoop it(n, L.Lp2);
+  const BlockRows br(n, L.Lp2);
   const int lmask = L.Lp2 - 1;
-  const long long stride = (long long)gridDim.x * kBlock;
   const int c0 = (threadIdx.x & lmask) * CW;
 
   T kV[CW];
@@ -162,27 +282,39 @@ __global__ void __launch_bounds__(kBlock) series_kernel(const SolveArgs a) {
                          : Vin + (size_t)(p + 1 - b - a.no_v0) * n;
   }
 
-  // ---- k = 1: S = D = V -----------------------------------------------------------------------------
+  // ---- setup pass: CSR checks, A_1 = A - xi I, and k = 1: S = D = V ---------------------------------
   int bad = 0;
+  unsigned long long epoch = 0;  // grid barriers passed (thread 0)
   {
     T* V1 = static_cast<T*>(a.Vt[1]);
     T* D1 = static_cast<T*>(a.Dt[1]);
     unsigned long long mx = 0;
-    for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
-      const long long item = base + threadIdx.x;
-      const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
-      const bool act = row < n && lane < L.L;
+    for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
+      const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
+      const bool act = row < br.r1 && lane < L.L;
       T part = T(0);
       if (act) {
-        if (lane == 0) {  // CSR structure check: monotone rowptr inside [0, nnz]
+        if (lane == 0) {
           const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
-          if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) bad = 1;
+          if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) {
+            bad = 1;
+          } else {
+            bool shifted = false;
+            for (int q = b0; q < b1; ++q) {  // subtract xi once from the stored diagonal, in FP64
+              double v = (double)__ldg(vals + q);
+              if (!shifted && __ldg(a.colidx + q) == row) {
+                v -= sc.xi;
+                shifted = true;
+              }
+              A1[q] = (T)v;
+            }
+          }
         }
         T x[CW];
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
           x[j] = kSrc[j] ? kSrc[j][row] * kV[j] : T(0);
-          part += tabs(x[j]);
+          part += fabs(x[j]);
         }
         const size_t o = (size_t)row * L.ws + c0;
         VecIO<T, CW>::st(V1 + o, x);
@@ -192,17 +324,11 @@ __global__ void __launch_bounds__(kBlock) series_kernel(const SolveArgs a) {
       const T rs = group_sum(part, L.Lp2);
       if (act && lane == 0) umax(mx, (double)rs);
     }
-    const unsigned long long m0 = block_max_u64(mx);
-    const int anybad = __syncthreads_or(bad);
-    if (threadIdx.x == 0) {
-      slot_max(ctl, 0, 0, m0);
-      if (anybad) set_status(ctl, PHIC_INVALID_ARG);
-    }
+    warp_parts(wp, mx, 0ull, bad);
   }
-  if (!grid_sync(ctl, a.spin_ns)) return;
 
   // Loop state, meaningful in thread 0 only.
-  int phase = 0, k = 1, status = PHIC_OK;
+  int phase = 0, k = 1, status = PHIC_OK, e0 = 0;
   double c1 = INFINITY, c2 = 0.0, nS = 0.0;
   auto decide = [&]() {  // thread 0: evaluate  while c1 + c2 > tol ||S||  and prepare term k+1
     int go = 0;
@@ -224,15 +350,19 @@ __global__ void __launch_bounds__(kBlock) series_kernel(const SolveArgs a) {
     lc.k = k;
     lc.status = status;
   };
-  if (threadIdx.x == 0) {
-    status = read_status(ctl);
-    c2 = slot_get(ctl, 0, 0);
-    nS = c2;
-    decide();
-  }
-  __syncthreads();
+  if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, 0, wp); },
+                      [&] {
+                        status = read_status(ctl);
+                        c2 = slot_get(ctl, 0, 0);
+                        nS = c2;
+                        e0 = scale_exponent(c2);  // norms of later terms are carried in FP32 scaled by 2^-e0
+                        set_norm_scale(lc, e0);
+                        decide();
+                      }))
+    return;
 
   // ---- k >= 2:  V <- V Jsh;  D <- A_1 D (I kron T/s) + V;  S <- S + D/k!  (divided by k!) ----------
+  const T xi = (T)sc.xi;
   while (lc.go) {
     const int kk = lc.k;
     ++phase;
@@ -244,66 +374,65 @@ __global__ void __launch_bounds__(kBlock) series_kernel(const SolveArgs a) {
       kA[j] = tk.ka[kI[j]];
       kT[j] = tk.kt[kI[j]];
     }
-    const T xi = (T)sc.xi;
     const T* __restrict__ Vo = static_cast<const T*>(a.Vt[(kk - 1) & 1]);
     T* __restrict__ Vn = static_cast<T*>(a.Vt[kk & 1]);
     const T* __restrict__ Do = static_cast<const T*>(a.Dt[(kk - 1) & 1]);
     T* __restrict__ Dn = static_cast<T*>(a.Dt[kk & 1]);
     unsigned long long mD = 0, mS = 0;
-    for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
-      const long long item = base + threadIdx.x;
-      const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
-      const bool act = row < n && lane < L.L;
-      T pD = T(0), pS = T(0);
+    const int bias = lc.bias;
+    const float fscale = lc.fscale;
+    int nf = 0;
+    for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
+      const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
+      const bool act = row < br.r1 && lane < L.L;
+      float pD = 0.f, pS = 0.f;
       if (act) {
         const size_t o = (size_t)row * L.ws + c0;
         T acc[CW];
 #pragma unroll
         for (int j = 0; j < CW; ++j) acc[j] = T(0);
-        spmm_row<T, CW>(a.rowptr, a.colidx, vals, Do, L.ws, c0, row, n, acc, bad);
+        const bool diag = spmm_row<T, CW>(a.rowptr, a.colidx, A1, Do, L.ws, c0, row, n, acc, bad);
         T own[CW], vo[CW], sv[CW], vn[CW], dn[CW];
         VecIO<T, CW>::ld(Do + o, own);
         VecIO<T, CW>::ld(Vo + o, vo);
         VecIO<T, CW>::ld(S + o, sv);
+        if (!diag) {  // no stored diagonal: apply the shift explicitly
+#pragma unroll
+          for (int j = 0; j < CW; ++j) acc[j] = fma(-xi, own[j], acc[j]);
+        }
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
           // block b of the new V: -xi t_i/s times block b, plus alpha_i/s times block b-1 when b >= 2
           T v = kD[j] * vo[j];
           if (kUp[j]) v = fma(kA[j], Vo[o + j - r], v);
-          const T d = fma(fma(-xi, own[j], acc[j]), kT[j], v);
+          const T d = fma(acc[j], kT[j], v);
           const T sn = sv[j] + d;
           vn[j] = kLive[j] ? v : T(0);
           dn[j] = kLive[j] ? d : T(0);
           sv[j] = kLive[j] ? sn : T(0);
-          pD += tabs(dn[j]);
-          pS += tabs(sv[j]);
+          pD += norm_piece(dn[j], bias, fscale, nf);
+          pS += norm_piece(sv[j], bias, fscale, nf);
         }
         VecIO<T, CW>::st(Vn + o, vn);
         VecIO<T, CW>::st(Dn + o, dn);
         VecIO<T, CW>::st(S + o, sv);
       }
-      const T rD = group_sum(pD, L.Lp2), rS = group_sum(pS, L.Lp2);
+      const float rD = group_sum(pD, L.Lp2), rS = group_sum(pS, L.Lp2);
       if (act && lane == 0) {
-        umax(mD, (double)rD);
-        umax(mS, (double)rS);
+        fmax_bits(mD, rD);
+        fmax_bits(mS, rS);
       }
     }
-    const unsigned long long bD = block_max_u64(mD);
-    const unsigned long long bS = block_max_u64(mS);
-    const int anybad = __syncthreads_or(bad);
-    if (threadIdx.x == 0) {
-      slot_max(ctl, phase, 0, bD);
-      slot_max(ctl, phase, 1, bS);
-      if (anybad) set_status(ctl, PHIC_INVALID_ARG);
-    }
-    if (!grid_sync(ctl, a.spin_ns)) return;
-    if (threadIdx.x == 0) {
-      status = read_status(ctl);
-      c2 = slot_get(ctl, phase, 0);  // ||D_k||_inf / k!
-      nS = slot_get(ctl, phase, 1);
-      decide();
-    }
-    __syncthreads();
+    warp_parts(wp, mD, mS, bad, nf);
+    if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, phase, wp); },
+                        [&] {
+                          status = read_status(ctl);
+                          if (status == PHIC_OK && slot_nonfinite(ctl, phase)) status = PHIC_NONFINITE;
+                          c2 = slot_norm(ctl, phase, 0, e0);  // ||D_k||_inf / k!
+                          nS = slot_norm(ctl, phase, 1, e0);
+                          decide();
+                        }))
+      return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (lc.status != PHIC_OK) set_status(ctl, lc.status);
@@ -320,22 +449,24 @@ __global__ void __launch_bounds__(kBlock) series_kernel(const SolveArgs a) {
 namespace {
 // Block p of S Jt^j, column i, is sum_{a=1..p} S(:, (a, i)) (j alpha_i/s)^(p-a) / (p-a)!, because
 // Jt^j = exp(j J kron Delta / s) and (J^q)[a, p] = 1 exactly when a = p - q >= 1.
-__device__ void jt_power_coeffs(RecoverScalars& rs, const SolveArgs& a, int j) {
+template <typename T>
+__device__ void jt_power_coeffs(RecoverScalars<T>& rs, const SolveArgs& a, int j) {
   const int p = a.p, r = a.r;
   for (int idx = threadIdx.x; idx < p * r; idx += blockDim.x) {
     const int aa = 1 + idx / r, i = idx % r;
     const double x = (double)j * a.alpha[i] / rs.s_int;
     double c = 1.0;
     for (int q = 1; q <= p - aa; ++q) c = c * x / q;
-    rs.cj[aa][i] = c;
+    rs.cj[aa][i] = (T)c;
   }
 }
 }  // namespace
 
 template <typename T, int CW>
-__global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
-  __shared__ RecoverScalars sc;
+__global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) recover_kernel(const SolveArgs a) {
+  __shared__ RecoverScalars<T> sc;
   __shared__ LoopCtl lc;
+  __shared__ WarpParts wp;
   Ctl* ctl = a.ctlR;
   const int n = a.n, r = a.r, p = a.p;
   const TileLayout L = a.F_lay;
@@ -380,12 +511,12 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
   }
 
   const T* __restrict__ vals = static_cast<const T*>(a.vals);
+  const T* __restrict__ A1 = static_cast<const T*>(a.A1);
   const T* __restrict__ S = static_cast<const T*>(a.S);
   const T* __restrict__ Vin = static_cast<const T*>(a.Vin);
   T* __restrict__ E = static_cast<T*>(a.E);
-  const ItemLoop it(n, L.Lp2);
+  const BlockRows br(n, L.Lp2);
   const int lmask = L.Lp2 - 1;
-  const long long stride = (long long)gridDim.x * kBlock;
   const int c0 = (threadIdx.x & lmask) * CW;
   int kI[CW];
   bool kLive[CW], kBlkP[CW];
@@ -396,21 +527,21 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
     kLive[j] = c < L.w;
     kBlkP[j] = kLive[j] && c >= r;
     kI[j] = !kLive[j] ? 0 : (c < r ? c : c - r);
-    kMu[j] = (T)sc.mu[kI[j]];
+    kMu[j] = kLive[j] ? (T)sc.mu[kI[j]] : T(0);
     kTt[j] = (T)a.t[kI[j]];
   }
   int bad = 0;
   int phase = 0;
+  unsigned long long epoch = 0;  // grid barriers passed (thread 0)
 
   // ---- F = S(:, [blk 0, blk p]);  F(:,1:r) <- A F(:,1:r) T + v0 1^T (unshifted A, t undivided) -----
   {
     T* F = static_cast<T*>(a.Ft[0]);
     const T* v0 = a.no_v0 ? nullptr : Vin;
     unsigned long long mx = 0;
-    for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
-      const long long item = base + threadIdx.x;
-      const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
-      const bool act = row < n && lane < L.L;
+    for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
+      const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
+      const bool act = row < br.r1 && lane < L.L;
       T part = T(0);
       if (act) {
         T f[CW];
@@ -431,56 +562,57 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
             v = S[(size_t)row * ws_s + p * r + kI[j]];
           }
           f[j] = v;
-          part += tabs(v);
+          part += fabs(v);
         }
         VecIO<T, CW>::st(F + (size_t)row * L.ws + c0, f);
       }
       const T rs = group_sum(part, L.Lp2);
       if (act && lane == 0) umax(mx, (double)rs);
     }
-    const unsigned long long bm = block_max_u64(mx);
-    const int anybad = __syncthreads_or(bad);
-    if (threadIdx.x == 0) {
-      slot_max(ctl, phase, 0, bm);
-      if (anybad) set_status(ctl, PHIC_INVALID_ARG);
-    }
-    if (!grid_sync(ctl, a.spin_ns)) { finish(PHIC_TIMEOUT); return; }
+    warp_parts(wp, mx, 0ull, bad);
   }
   // thread-0 loop state
-  int status = PHIC_OK, k = 0;
+  int status = PHIC_OK, k = 0, e0 = 0;
   double cF = 0.0, c1 = 0.0, c2 = 0.0, nE = 0.0;
-  if (threadIdx.x == 0) {
-    status = read_status(ctl);
-    cF = slot_get(ctl, phase, 0);
-    lc.status = status;
+  if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, 0, wp); },
+                      [&] {
+                        status = read_status(ctl);
+                        cF = slot_get(ctl, 0, 0);
+                        lc.status = status;
+                      })) {
+    finish(PHIC_TIMEOUT);
+    return;
   }
-  __syncthreads();
   int cur = 0;
+  const T xi = (T)sc.xi;
+
+  // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||: next term
+  auto decide = [&]() {
+    int go = 0;
+    if (status == PHIC_OK && (!isfinite(c2) || !isfinite(nE))) status = PHIC_NONFINITE;
+    if (status == PHIC_OK && c1 + c2 > a.tol * nE) {
+      if (k >= a.max_terms) status = PHIC_TERM_CAP;
+      else {
+        k += 1;
+        c1 = c2;
+        go = 1;
+        for (int i = 0; i < r; ++i) sc.scale[i] = (T)(sc.tcF[i] / k);
+      }
+    }
+    lc.go = go;
+    lc.k = k;
+    lc.status = status;
+  };
 
   // ---- for j = 1 : s-1 ------------------------------------------------------------------------------
   for (int jstep = 1; jstep <= sc.s_int - 1 && lc.status == PHIC_OK; ++jstep) {
-    // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||
-    auto decide = [&]() {
-      int go = 0;
-      if (status == PHIC_OK && (!isfinite(c2) || !isfinite(nE))) status = PHIC_NONFINITE;
-      if (status == PHIC_OK && c1 + c2 > a.tol * nE) {
-        if (k >= a.max_terms) status = PHIC_TERM_CAP;
-        else {
-          k += 1;
-          c1 = c2;
-          go = 1;
-          for (int i = 0; i < r; ++i) sc.scale[i] = sc.tcF[i] / k;
-        }
-      }
-      lc.go = go;
-      lc.k = k;
-      lc.status = status;
-    };
     if (threadIdx.x == 0) {
       k = 0;
       c1 = INFINITY;
       c2 = cF;
       nE = cF;
+      e0 = scale_exponent(cF);  // norms of this step's terms are carried in FP32 scaled by 2^-e0
+      set_norm_scale(lc, e0);
       decide();
     }
     __syncthreads();
@@ -490,22 +622,23 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
       slot_reset(ctl, phase);
       T kS[CW];
 #pragma unroll
-      for (int j = 0; j < CW; ++j) kS[j] = kLive[j] ? (T)sc.scale[kI[j]] : T(0);
-      const T xi = (T)sc.xi;
+      for (int j = 0; j < CW; ++j) kS[j] = kLive[j] ? sc.scale[kI[j]] : T(0);
       const T* __restrict__ Fo = static_cast<const T*>(a.Ft[cur]);
       T* __restrict__ Fn = static_cast<T*>(a.Ft[cur ^ 1]);
       unsigned long long mF = 0, mE = 0;
-      for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
-        const long long item = base + threadIdx.x;
-        const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
-        const bool act = row < n && lane < L.L;
-        T pF = T(0), pE = T(0);
+      const int bias = lc.bias;
+      const float fscale = lc.fscale;
+      int nf = 0;
+      for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
+        const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
+        const bool act = row < br.r1 && lane < L.L;
+        float pF = 0.f, pE = 0.f;
         if (act) {
           const size_t o = (size_t)row * L.ws + c0;
           T acc[CW];
 #pragma unroll
           for (int j = 0; j < CW; ++j) acc[j] = T(0);
-          spmm_row<T, CW>(a.rowptr, a.colidx, vals, Fo, L.ws, c0, row, n, acc, bad);
+          const bool diag = spmm_row<T, CW>(a.rowptr, a.colidx, A1, Fo, L.ws, c0, row, n, acc, bad);
           T own[CW], e[CW], fn[CW];
           VecIO<T, CW>::ld(Fo + o, own);
           if (kk == 1) {
@@ -514,41 +647,41 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
           } else {
             VecIO<T, CW>::ld(E + o, e);
           }
+          if (!diag) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j) acc[j] = fma(-xi, own[j], acc[j]);
+          }
 #pragma unroll
           for (int j = 0; j < CW; ++j) {
             // F <- A_1 F T / k;  E <- E + F
-            const T f = fma(-xi, own[j], acc[j]) * kS[j];
+            const T f = acc[j] * kS[j];
             fn[j] = f;
             e[j] += f;
-            pF += tabs(f);
-            pE += tabs(e[j]);
+            pF += norm_piece(f, bias, fscale, nf);
+            pE += norm_piece(e[j], bias, fscale, nf);
           }
           VecIO<T, CW>::st(Fn + o, fn);
           VecIO<T, CW>::st(E + o, e);
         }
-        const T rF = group_sum(pF, L.Lp2), rE = group_sum(pE, L.Lp2);
+        const float rF = group_sum(pF, L.Lp2), rE = group_sum(pE, L.Lp2);
         if (act && lane == 0) {
-          umax(mF, (double)rF);
-          umax(mE, (double)rE);
+          fmax_bits(mF, rF);
+          fmax_bits(mE, rE);
         }
       }
-      const unsigned long long bF = block_max_u64(mF);
-      const unsigned long long bE = block_max_u64(mE);
-      const int anybad = __syncthreads_or(bad);
-      if (threadIdx.x == 0) {
-        slot_max(ctl, phase, 0, bF);
-        slot_max(ctl, phase, 1, bE);
-        if (anybad) set_status(ctl, PHIC_INVALID_ARG);
-      }
-      if (!grid_sync(ctl, a.spin_ns)) { finish(PHIC_TIMEOUT); return; }
+      warp_parts(wp, mF, mE, bad, nf);
       cur ^= 1;
-      if (threadIdx.x == 0) {
-        status = read_status(ctl);
-        c2 = slot_get(ctl, phase, 0);
-        nE = slot_get(ctl, phase, 1);
-        decide();
+      if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, phase, wp); },
+                          [&] {
+                            status = read_status(ctl);
+                            if (status == PHIC_OK && slot_nonfinite(ctl, phase)) status = PHIC_NONFINITE;
+                            c2 = slot_norm(ctl, phase, 0, e0);
+                            nE = slot_norm(ctl, phase, 1, e0);
+                            decide();
+                          })) {
+        finish(PHIC_TIMEOUT);
+        return;
       }
-      __syncthreads();
     }
     if (leader) {
       rec_terms += lc.k;
@@ -564,10 +697,9 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
     {
       T* __restrict__ F = static_cast<T*>(a.Ft[cur]);
       unsigned long long mx = 0;
-      for (long long base = (long long)blockIdx.x * kBlock; base < it.total; base += stride) {
-        const long long item = base + threadIdx.x;
-        const int row = (int)(item >> it.shift), lane = (int)(item & lmask);
-        const bool act = row < n && lane < L.L;
+      for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
+        const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
+        const bool act = row < br.r1 && lane < L.L;
         T part = T(0);
         if (act) {
           const size_t o = (size_t)row * L.ws + c0;
@@ -579,25 +711,26 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
             if (kBlkP[j]) {
               const int i = kI[j];
               const T* srow = S + (size_t)row * ws_s;
-              for (int aa = 1; aa <= p; ++aa) v = fma(srow[aa * r + i], (T)sc.cj[aa][i], v);
+              for (int aa = 1; aa <= p; ++aa) v = fma(srow[aa * r + i], sc.cj[aa][i], v);
             }
             e[j] = kLive[j] ? v : T(0);
-            part += tabs(e[j]);
+            part += fabs(e[j]);
           }
           VecIO<T, CW>::st(F + o, e);
         }
         const T rs = group_sum(part, L.Lp2);
         if (act && lane == 0) umax(mx, (double)rs);
       }
-      const unsigned long long bm = block_max_u64(mx);
-      if (threadIdx.x == 0) slot_max(ctl, phase, 0, bm);
-      if (!grid_sync(ctl, a.spin_ns)) { finish(PHIC_TIMEOUT); return; }
-      if (threadIdx.x == 0) {
-        cF = slot_get(ctl, phase, 0);
-        status = read_status(ctl);
-        lc.status = status;
+      warp_parts(wp, mx, 0ull, 0);
+      if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, phase, wp); },
+                          [&] {
+                            cF = slot_get(ctl, phase, 0);
+                            status = read_status(ctl);
+                            lc.status = status;
+                          })) {
+        finish(PHIC_TIMEOUT);
+        return;
       }
-      __syncthreads();
     }
   }
 
@@ -606,6 +739,7 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
     const T* __restrict__ F = static_cast<const T*>(a.Ft[cur]);
     T* __restrict__ W = static_cast<T*>(a.W);
     const long long total = (long long)n * r;
+    const long long stride = (long long)gridDim.x * kBlock;
     for (long long idx = (long long)blockIdx.x * kBlock + threadIdx.x; idx < total; idx += stride) {
       const int i = (int)(idx / n), row = (int)(idx - (long long)i * n);
       const T* frow = F + (size_t)row * L.ws;
@@ -617,7 +751,6 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const SolveArgs a) {
 
 // ---------------------------------------------------------------------------------------------------
 namespace {
-
 
 template <typename K>
 cudaError_t coop_launch(K kernel, long long items, int max_per_sm, const SolveArgs& a, cudaStream_t st,
@@ -674,10 +807,10 @@ cudaError_t launch_recover(const SolveArgs& a, int prec, cudaStream_t st, int* g
 TileLayout pick_layout(int w) {
   TileLayout t;
   t.w = w;
-  if (w % 4 == 0 && w / 4 <= 32) {
+  if (PHIC_CW_MAX >= 4 && w % 4 == 0 && w / 4 <= 32) {
     t.cw = 4;
     t.ws = w;
-  } else if (w % 2 == 0 && w / 2 <= 32) {
+  } else if (PHIC_CW_MAX >= 2 && w % 2 == 0 && w / 2 <= 32) {
     t.cw = 2;
     t.ws = w;
   } else if (w <= 32) {

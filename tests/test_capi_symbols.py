@@ -40,9 +40,9 @@ def test_host_queries_without_gpu():
 
     lib = capi.load(build_if_missing=True)
     out = ctypes.c_size_t(0)
-    assert lib.phic_solve_workspace_size(262144, 3, 2, 0, ctypes.byref(out)) == 0
-    # two 8-wide series tiles... : V x2, D x2, S (8 doubles/row) + F x2, E (4 doubles/row) + control
-    assert out.value >= 262144 * 8 * (5 * 8 + 3 * 4)
-    assert lib.phic_solve_workspace_size(10, 16, 1, 0, ctypes.byref(out)) == capi.PHIC_INVALID_ARG
+    assert lib.phic_solve_workspace_size(262144, 1810432, 3, 2, 0, ctypes.byref(out)) == 0
+    # A_1 copy (nnz doubles) + V x2, D x2, S (8 doubles/row) + F x2, E (4 doubles/row) + control
+    assert out.value >= 1810432 * 8 + 262144 * 8 * (5 * 8 + 3 * 4)
+    assert lib.phic_solve_workspace_size(10, 50, 16, 1, 0, ctypes.byref(out)) == capi.PHIC_INVALID_ARG
     assert lib.phic_select_workspace_size(1000, 61, ctypes.byref(out)) == 0
     assert out.value >= 1000 * 62 * 8

@@ -85,7 +85,7 @@ def test_host_argument_checks():
     c32 = A.astype(torch.float32).struct()
     t1 = (ctypes.c_double * 1)(1.0)
     W = torch.empty((1, A.n), dtype=torch.float64, device="cuda")
-    ws = torch.empty(api.solve_workspace_bytes(A.n, 2, 1, 0), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(api.solve_workspace_bytes(A.n, A.nnz, 2, 1, 0), dtype=torch.uint8, device="cuda")
     assert lib.phic_solve(ctypes.byref(c32), 2, 1, V.data_ptr(), t1, t1, 1e-10, P.data_ptr(), 0, 0, W.data_ptr(),
                           ws.data_ptr(), ws.numel(), None, 0, None) == capi.PHIC_INVALID_ARG  # prec mismatch
     with pytest.raises(capi.PhicError):  # r above the limit
