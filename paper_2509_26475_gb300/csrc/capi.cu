@@ -44,7 +44,7 @@ SelectLayout select_layout(int64_t n, int m) {
 }
 
 struct SolveLayout {
-  size_t ctlS, ctlR, state, A1, Vt[2], Dt[2], S, Ft[2], E, total;
+  size_t ctlS, ctlR, state, A1, rowflag, Vt[2], Dt[2], S, Ft[2], E, total;
   TileLayout sl, fl;
 };
 SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec) {
@@ -59,7 +59,8 @@ SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec) {
   L.ctlR = off; off += align_up(sizeof(Ctl));
   L.state = off; off += align_up(sizeof(SolveState));
   const size_t head = off;  // control blocks and state: zeroed before each solve
-  L.A1 = off; off += align_up((size_t)(nnz > 0 ? nnz : 1) * es);
+  L.A1 = off; off += align_up((size_t)(nnz > 0 ? nnz : 1) * 2 * es);  // (column, value) entries
+  L.rowflag = off; off += align_up((size_t)n);
   for (int q = 0; q < 2; ++q) { L.Vt[q] = off; off += tileS; }
   for (int q = 0; q < 2; ++q) { L.Dt[q] = off; off += tileS; }
   L.S = off; off += tileS;
@@ -179,6 +180,7 @@ phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, c
   a.colidx = A->colidx;
   a.vals = A->values;
   a.A1 = base + L.A1;
+  a.rowflag = reinterpret_cast<unsigned char*>(base + L.rowflag);
   a.Vin = V;
   a.W = W;
   a.p = p;
@@ -294,6 +296,7 @@ extern "C" phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t 
   a.colidx = A->colidx;
   a.vals = A->values;
   a.A1 = base + L.A1;
+  a.rowflag = reinterpret_cast<unsigned char*>(base + L.rowflag);
   a.Vin = V;
   a.W = W;
   a.p = p;

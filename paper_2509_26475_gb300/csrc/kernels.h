@@ -20,10 +20,24 @@ TileLayout pick_layout(int w);
 struct SolveState {
   int s_int;
   int series_terms;
-  int pad[2];
+  int eA;      // B = A_1 2^-eA has infinity norm below 1
+  int nodiag;  // some row stores no diagonal entry (its shift is applied explicitly)
   double xi;
   double s;
   double pad2[4];
+};
+
+// Entry of the solve's copy of A_1 = A - xi I, scaled by 2^-eA: column and value in one aligned load.
+template <typename T>
+struct alignas(2 * sizeof(T)) CsrEnt {
+  int col;
+  int pad_for_double;
+  T v;
+};
+template <>
+struct alignas(8) CsrEnt<float> {
+  int col;
+  float v;
 };
 
 struct SolveArgs {
@@ -31,7 +45,8 @@ struct SolveArgs {
   const int* rowptr;
   const int* colidx;
   const void* vals;
-  void* A1;  // workspace copy of the values with xi subtracted from the stored diagonal (A_1 = A - xi I)
+  void* A1;               // CsrEnt<T>[nnz]: columns and values of B = (A - xi I) 2^-eA
+  unsigned char* rowflag; // [n] 1 where the row stores no diagonal entry
   const void* Vin;
   void* W;
   int p, r, no_v0;

@@ -18,21 +18,25 @@
 // a warp, so the row sums of |x| for the infinity norm are shuffle reductions.  A thread keeps the
 // same lane in every pass, so its per-column constants live in registers.
 //
-// On GB300 the FP64 pipe (2 FMA/clk/SM) bounds these kernels, so the per-element FP64 work is kept to
-// the products with A_1, one scale and one accumulation: the infinity norms of the terms, which only
-// decide when a Taylor loop stops, are summed in FP32 from the high words of the doubles (norm_piece).
+// GB300 cost model.  FP64 arithmetic runs at 2 FMA/clk/SM and shares its issue path with the load,
+// store and shuffle instructions (one memory instruction costs about 1.25 FP64 FMA there, integer
+// and FP32 work cost nothing there).  Hence:
+//   - the operator is held as B = (A - xi I) 2^-eA in (column, value) pairs, one 16-byte load per
+//     nonzero, with ||B||_inf < 1 (2^-eA is an exact scaling);
+//   - the recovery carries G_k = B^k F_0 unscaled and F_k = c_k G_k with per-column FP64 scalars
+//     c_k = (t_i 2^eA / s)^k / k! kept by thread 0, so E <- E + F_k is one FMA per element;
+//   - the infinity norms that decide when a Taylor loop stops are summed in FP32 from the high words
+//     of the doubles (norm_piece), with no FP64 instruction.
 #include <math.h>
 
 #include "common.cuh"
 #include "kernels.h"
 
-// Tile shape of the block kernels: widest column chunk a lane takes (1, 2 or 4) and the minimum
-// resident blocks per SM requested from the register allocator.
+// Tile shape of the block kernels: widest column chunk a lane takes (1, 2 or 4).  Two columns per lane
+// with two (narrow tiles) or three (tiles of 8 or more columns) resident blocks per SM measured fastest
+// on GB300 for FP64: more warps hide the gathers, and wider chunks need registers that cost residency.
 #ifndef PHIC_CW_MAX
-#define PHIC_CW_MAX 4
-#endif
-#ifndef PHIC_MIN_BLOCKS
-#define PHIC_MIN_BLOCKS 1
+#define PHIC_CW_MAX 2
 #endif
 
 namespace phic {
@@ -59,8 +63,8 @@ __device__ __forceinline__ void umax(unsigned long long& m, double v) {
   m = u > m ? u : m;
 }
 
-// Per-warp maxima of two norms and the bad-index flag; thread 0 folds them into the grid slots
-// inside the barrier.
+// Per-warp maxima of two values and the bad-index / non-finite flags; thread 0 folds them into the
+// grid slots inside the barrier.
 struct WarpParts {
   unsigned long long a[kBlock / 32], b[kBlock / 32];
   int bad[kBlock / 32], nonfinite[kBlock / 32];
@@ -114,45 +118,29 @@ __device__ __forceinline__ int scale_exponent(double ref) {
   return (ref > 0.0 && isfinite(ref)) ? ilogb(ref) : 0;
 }
 
-// acc[j] += sum_q M(row, col_q) X(col_q, c0 + j) over the row's nonzeros, four nonzeros at a time so
-// that their gathers are in flight together.  A column index outside [0, n) is flagged and replaced by
-// the row itself with a zero weight, so no address outside X is read and the loop has no branch on data.
-// Returns whether the row stores a diagonal entry.
+// acc[j] += sum_q B(row, col_q) X(col_q, c0 + j) over the row's stored entries, four at a time so that
+// their gathers are in flight together.  Columns were checked when the entries were written.
 template <typename T, int CW>
-__device__ __forceinline__ bool spmm_row(const int* __restrict__ rowptr, const int* __restrict__ colidx,
-                                         const T* __restrict__ vals, const T* __restrict__ X, int ws, int c0,
-                                         int row, int n, T (&acc)[CW], int& bad) {
+__device__ __forceinline__ void spmm_ent(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent,
+                                         const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW]) {
   const int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
-  bool diag = false;
   for (int q0 = beg; q0 < end; q0 += 4) {
     const int cnt = end - q0;
-    int col[4];
-    T av[4];
+    CsrEnt<T> e[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      col[u] = row;
-      av[u] = T(0);
-      if (u < cnt) {
-        const int c = __ldg(colidx + q0 + u);
-        const bool ok = (unsigned)c < (unsigned)n;
-        bad |= !ok;
-        diag |= (c == row);
-        col[u] = ok ? c : row;
-        av[u] = ok ? __ldg(vals + q0 + u) : T(0);
-      }
-    }
+    for (int u = 0; u < 4; ++u)
+      if (u < cnt) e[u] = ent[q0 + u];
     T x[4][CW];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (u < cnt) VecIO<T, CW>::ld(X + (size_t)col[u] * ws + c0, x[u]);
+      if (u < cnt) VecIO<T, CW>::ld(X + (size_t)e[u].col * ws + c0, x[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u)
       if (u < cnt) {
 #pragma unroll
-        for (int j = 0; j < CW; ++j) acc[j] = fma(av[u], x[u][j], acc[j]);
+        for (int j = 0; j < CW; ++j) acc[j] = fma(e[u].v, x[u][j], acc[j]);
       }
   }
-  return diag;
 }
 
 // |x| 2^-e0 as an FP32 value, for the infinity-norm sums that feed the truncation test.  For a double
@@ -198,15 +186,16 @@ struct SeriesTerm {
 
 struct SeriesScalars {
   double xi, tc[PHIC_MAX_R], cA[PHIC_MAX_R], cD[PHIC_MAX_R], cV[PHIC_MAX_R];
-  int s_int, bad;
+  int s_int, bad, eA, nodiag;
 };
 
 template <typename T>
 struct RecoverScalars {
-  double xi, tcF[PHIC_MAX_R], mu[PHIC_MAX_R];
-  T scale[PHIC_MAX_R];
+  double xi, tB[PHIC_MAX_R], mu[PHIC_MAX_R], c[PHIC_MAX_R];
+  T coef[PHIC_MAX_R];
+  float fcoef[PHIC_MAX_R];
   T cj[PHIC_MAX_P + 1][PHIC_MAX_R];
-  int s_int, series_terms, status;
+  int s_int, series_terms, status, eA, nodiag;
 };
 
 }  // namespace
@@ -214,12 +203,12 @@ struct RecoverScalars {
 // ===================================================================================================
 // Block series (Algorithm 3: setup and the first while loop)
 // ===================================================================================================
-// The recurrence is carried divided by k!: with X = A_1 (I kron T/s),
+// The recurrence is carried divided by k!: with X = A_1 (I kron T/s) = 2^eA B (I kron T/s),
 //   V~_k = V~_{k-1} Jsh / k,   D~_k = X D~_{k-1} / k + V~_k,   S = sum_k D~_k,   c2 = ||D~_k||_inf,
 // which equals the paper's D_k / k! and V_k / k! term by term but never holds the growing X^k D_1,
 // which would overflow FP32 (and, for a large ||X||, FP64) long before the terms become small.
-template <typename T, int CW>
-__global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const SolveArgs a) {
+template <typename T, int CW, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) series_kernel(const SolveArgs a) {
   __shared__ SeriesScalars sc;
   __shared__ LoopCtl lc;
   __shared__ SeriesTerm<T> tk;
@@ -257,7 +246,7 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
   if (a.fault && blockIdx.x == 0 && gridDim.x > 1) return;  // test hook: never arrive at the barrier
 
   const T* __restrict__ vals = static_cast<const T*>(a.vals);
-  T* __restrict__ A1 = static_cast<T*>(a.A1);
+  CsrEnt<T>* __restrict__ ent = static_cast<CsrEnt<T>*>(a.A1);
   const T* __restrict__ Vin = static_cast<const T*>(a.Vin);
   T* __restrict__ S = static_cast<T*>(a.S);
   const BlockRows br(n, L.Lp2);
@@ -281,11 +270,60 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
               : (b == 0) ? (a.no_v0 ? nullptr : Vin)
                          : Vin + (size_t)(p + 1 - b - a.no_v0) * n;
   }
-
-  // ---- setup pass: CSR checks, A_1 = A - xi I, and k = 1: S = D = V ---------------------------------
   int bad = 0;
   unsigned long long epoch = 0;  // grid barriers passed (thread 0)
+
+  // ---- setup pass 1: CSR checks, ||A - xi I||_inf, rows without a stored diagonal -------------------
   {
+    unsigned long long mx = 0;
+    int nodiag = 0;
+    for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
+      const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
+      if (row < br.r1 && lane == 0) {
+        const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
+        if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) {
+          bad = 1;
+        } else {
+          bool shifted = false;
+          double rs = 0.0;
+          for (int q = b0; q < b1; ++q) {
+            const int col = __ldg(a.colidx + q);
+            if ((unsigned)col >= (unsigned)n) { bad = 1; continue; }
+            double v = (double)__ldg(vals + q);
+            if (!shifted && col == row) {
+              v -= sc.xi;
+              shifted = true;
+            }
+            rs += fabs(v);
+          }
+          if (!shifted) rs += fabs(sc.xi);
+          a.rowflag[row] = shifted ? 0 : 1;
+          nodiag |= !shifted;
+          umax(mx, rs);
+        }
+      }
+    }
+    warp_parts(wp, mx, (unsigned long long)nodiag, bad);
+  }
+  if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, 0, wp); },
+                      [&] {
+                        const double na = slot_get(ctl, 0, 0);
+                        sc.eA = (na > 0.0 && isfinite(na)) ? ilogb(na) + 1 : 0;  // ||B||_inf < 1
+                        sc.nodiag = slot_get(ctl, 0, 1) != 0.0;
+                        lc.status = read_status(ctl);
+                      }))
+    return;
+  if (lc.status != PHIC_OK) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.state->s_int = sc.s_int;
+      a.state->series_terms = 1;
+    }
+    return;
+  }
+
+  // ---- setup pass 2: entries of B = (A - xi I) 2^-eA, and k = 1: S = D = V -------------------------
+  {
+    const double scaleB = ldexp(1.0, -sc.eA);
     T* V1 = static_cast<T*>(a.Vt[1]);
     T* D1 = static_cast<T*>(a.Dt[1]);
     unsigned long long mx = 0;
@@ -296,18 +334,18 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
       if (act) {
         if (lane == 0) {
           const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
-          if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) {
-            bad = 1;
-          } else {
-            bool shifted = false;
-            for (int q = b0; q < b1; ++q) {  // subtract xi once from the stored diagonal, in FP64
-              double v = (double)__ldg(vals + q);
-              if (!shifted && __ldg(a.colidx + q) == row) {
-                v -= sc.xi;
-                shifted = true;
-              }
-              A1[q] = (T)v;
+          bool shifted = false;
+          for (int q = b0; q < b1; ++q) {  // subtract xi once from the stored diagonal, in FP64
+            const int col = __ldg(a.colidx + q);
+            double v = (double)__ldg(vals + q);
+            if (!shifted && col == row) {
+              v -= sc.xi;
+              shifted = true;
             }
+            CsrEnt<T> e;
+            e.col = col;
+            e.v = (T)(v * scaleB);
+            ent[q] = e;
           }
         }
         T x[CW];
@@ -324,11 +362,11 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
       const T rs = group_sum(part, L.Lp2);
       if (act && lane == 0) umax(mx, (double)rs);
     }
-    warp_parts(wp, mx, 0ull, bad);
+    warp_parts(wp, mx, 0ull, 0);
   }
 
   // Loop state, meaningful in thread 0 only.
-  int phase = 0, k = 1, status = PHIC_OK, e0 = 0;
+  int phase = 1, k = 1, status = PHIC_OK, e0 = 0;
   double c1 = INFINITY, c2 = 0.0, nS = 0.0;
   auto decide = [&]() {  // thread 0: evaluate  while c1 + c2 > tol ||S||  and prepare term k+1
     int go = 0;
@@ -339,10 +377,11 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
         k += 1;
         c1 = c2;
         go = 1;
+        const double sB = ldexp(1.0, sc.eA);
         for (int i = 0; i < r; ++i) {
           tk.kd[i] = (T)(sc.cD[i] / k);
           tk.ka[i] = (T)(sc.cA[i] / k);
-          tk.kt[i] = (T)(sc.tc[i] / k);
+          tk.kt[i] = (T)(sc.tc[i] * sB / k);
         }
       }
     }
@@ -350,10 +389,11 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
     lc.k = k;
     lc.status = status;
   };
-  if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, 0, wp); },
+  slot_reset(ctl, phase);
+  if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, 1, wp); },
                       [&] {
                         status = read_status(ctl);
-                        c2 = slot_get(ctl, 0, 0);
+                        c2 = slot_get(ctl, 1, 0);
                         nS = c2;
                         e0 = scale_exponent(c2);  // norms of later terms are carried in FP32 scaled by 2^-e0
                         set_norm_scale(lc, e0);
@@ -362,7 +402,8 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
     return;
 
   // ---- k >= 2:  V <- V Jsh;  D <- A_1 D (I kron T/s) + V;  S <- S + D/k!  (divided by k!) ----------
-  const T xi = (T)sc.xi;
+  const T xiB = (T)(-sc.xi * ldexp(1.0, -sc.eA));  // explicit shift for rows without a stored diagonal
+  const bool nodiag = sc.nodiag != 0;
   while (lc.go) {
     const int kk = lc.k;
     ++phase;
@@ -391,15 +432,16 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
         T acc[CW];
 #pragma unroll
         for (int j = 0; j < CW; ++j) acc[j] = T(0);
-        const bool diag = spmm_row<T, CW>(a.rowptr, a.colidx, A1, Do, L.ws, c0, row, n, acc, bad);
-        T own[CW], vo[CW], sv[CW], vn[CW], dn[CW];
-        VecIO<T, CW>::ld(Do + o, own);
+        spmm_ent<T, CW>(a.rowptr, ent, Do, L.ws, c0, row, acc);
+        if (nodiag && a.rowflag[row]) {  // no stored diagonal: apply the shift explicitly
+          T own[CW];
+          VecIO<T, CW>::ld(Do + o, own);
+#pragma unroll
+          for (int j = 0; j < CW; ++j) acc[j] = fma(xiB, own[j], acc[j]);
+        }
+        T vo[CW], sv[CW], vn[CW], dn[CW];
         VecIO<T, CW>::ld(Vo + o, vo);
         VecIO<T, CW>::ld(S + o, sv);
-        if (!diag) {  // no stored diagonal: apply the shift explicitly
-#pragma unroll
-          for (int j = 0; j < CW; ++j) acc[j] = fma(-xi, own[j], acc[j]);
-        }
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
           // block b of the new V: -xi t_i/s times block b, plus alpha_i/s times block b-1 when b >= 2
@@ -423,7 +465,7 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
         fmax_bits(mS, rS);
       }
     }
-    warp_parts(wp, mD, mS, bad, nf);
+    warp_parts(wp, mD, mS, 0, nf);
     if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, phase, wp); },
                         [&] {
                           status = read_status(ctl);
@@ -440,6 +482,8 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) series_kernel(const S
     a.state->series_terms = lc.k;
     a.state->xi = sc.xi;
     a.state->s = a.params->s;
+    a.state->eA = sc.eA;
+    a.state->nodiag = sc.nodiag;
   }
 }
 
@@ -462,8 +506,10 @@ __device__ void jt_power_coeffs(RecoverScalars<T>& rs, const SolveArgs& a, int j
 }
 }  // namespace
 
-template <typename T, int CW>
-__global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) recover_kernel(const SolveArgs a) {
+// Recovery step j: F_k = A_1 F_{k-1} T / (s k) is carried as F_k = c_k G_k with G_k = B G_{k-1},
+// G_0 = F and c_k = c_{k-1} t_i 2^eA / (s k) per column, so that E <- E + F_k is fma(c_k, G_k, E).
+template <typename T, int CW, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) recover_kernel(const SolveArgs a) {
   __shared__ RecoverScalars<T> sc;
   __shared__ LoopCtl lc;
   __shared__ WarpParts wp;
@@ -477,9 +523,12 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) recover_kernel(const 
     sc.s_int = a.state->s_int;
     sc.series_terms = a.state->series_terms;
     sc.xi = a.state->xi;
+    sc.eA = a.state->eA;
+    sc.nodiag = a.state->nodiag;
     if (sc.status == PHIC_OK) {
+      const double sB = ldexp(1.0, sc.eA);
       for (int i = 0; i < r; ++i) {
-        sc.tcF[i] = a.t[i] / sc.s_int;                 // T <- I_2 kron T/s
+        sc.tB[i] = a.t[i] * sB / sc.s_int;            // T <- I_2 kron T/s, times 2^eA for B
         sc.mu[i] = exp(sc.xi * a.t[i] / sc.s_int);     // mu <- I_2 kron mu
       }
     }
@@ -511,7 +560,7 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) recover_kernel(const 
   }
 
   const T* __restrict__ vals = static_cast<const T*>(a.vals);
-  const T* __restrict__ A1 = static_cast<const T*>(a.A1);
+  const CsrEnt<T>* __restrict__ ent = static_cast<const CsrEnt<T>*>(a.A1);
   const T* __restrict__ S = static_cast<const T*>(a.S);
   const T* __restrict__ Vin = static_cast<const T*>(a.Vin);
   T* __restrict__ E = static_cast<T*>(a.E);
@@ -584,7 +633,8 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) recover_kernel(const 
     return;
   }
   int cur = 0;
-  const T xi = (T)sc.xi;
+  const T xiB = (T)(-sc.xi * ldexp(1.0, -sc.eA));
+  const bool nodiag = sc.nodiag != 0;
 
   // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||: next term
   auto decide = [&]() {
@@ -596,7 +646,11 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) recover_kernel(const 
         k += 1;
         c1 = c2;
         go = 1;
-        for (int i = 0; i < r; ++i) sc.scale[i] = (T)(sc.tcF[i] / k);
+        for (int i = 0; i < r; ++i) {
+          sc.c[i] = k == 1 ? sc.tB[i] : sc.c[i] * sc.tB[i] / k;  // c_k = (t_i 2^eA / s)^k / k!
+          sc.coef[i] = (T)sc.c[i];
+          sc.fcoef[i] = (float)sc.c[i];
+        }
       }
     }
     lc.go = go;
@@ -620,11 +674,15 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) recover_kernel(const 
       const int kk = lc.k;
       ++phase;
       slot_reset(ctl, phase);
-      T kS[CW];
+      T kC[CW];
+      float kF[CW];
 #pragma unroll
-      for (int j = 0; j < CW; ++j) kS[j] = kLive[j] ? sc.scale[kI[j]] : T(0);
-      const T* __restrict__ Fo = static_cast<const T*>(a.Ft[cur]);
-      T* __restrict__ Fn = static_cast<T*>(a.Ft[cur ^ 1]);
+      for (int j = 0; j < CW; ++j) {
+        kC[j] = kLive[j] ? sc.coef[kI[j]] : T(0);
+        kF[j] = kLive[j] ? sc.fcoef[kI[j]] : 0.f;
+      }
+      const T* __restrict__ Go = static_cast<const T*>(a.Ft[cur]);
+      T* __restrict__ Gn = static_cast<T*>(a.Ft[cur ^ 1]);
       unsigned long long mF = 0, mE = 0;
       const int bias = lc.bias;
       const float fscale = lc.fscale;
@@ -638,29 +696,30 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) recover_kernel(const 
           T acc[CW];
 #pragma unroll
           for (int j = 0; j < CW; ++j) acc[j] = T(0);
-          const bool diag = spmm_row<T, CW>(a.rowptr, a.colidx, A1, Fo, L.ws, c0, row, n, acc, bad);
-          T own[CW], e[CW], fn[CW];
-          VecIO<T, CW>::ld(Fo + o, own);
-          if (kk == 1) {
+          spmm_ent<T, CW>(a.rowptr, ent, Go, L.ws, c0, row, acc);
+          const bool shift_row = nodiag && a.rowflag[row];
+          T e[CW];
+          if (kk == 1 || shift_row) {
+            T own[CW];
+            VecIO<T, CW>::ld(Go + o, own);
+            if (shift_row) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) e[j] = own[j];  // E = F at the start of the step
-          } else {
-            VecIO<T, CW>::ld(E + o, e);
-          }
-          if (!diag) {
+              for (int j = 0; j < CW; ++j) acc[j] = fma(xiB, own[j], acc[j]);
+            }
+            if (kk == 1) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) acc[j] = fma(-xi, own[j], acc[j]);
+              for (int j = 0; j < CW; ++j) e[j] = own[j];  // E = F at the start of the step
+            }
           }
+          if (kk != 1) VecIO<T, CW>::ld(E + o, e);
 #pragma unroll
           for (int j = 0; j < CW; ++j) {
-            // F <- A_1 F T / k;  E <- E + F
-            const T f = acc[j] * kS[j];
-            fn[j] = f;
-            e[j] += f;
-            pF += norm_piece(f, bias, fscale, nf);
+            // F_k = c_k G_k;  E <- E + F_k
+            e[j] = fma(kC[j], acc[j], e[j]);
+            pF += kF[j] * norm_piece(acc[j], bias, fscale, nf);
             pE += norm_piece(e[j], bias, fscale, nf);
           }
-          VecIO<T, CW>::st(Fn + o, fn);
+          VecIO<T, CW>::st(Gn + o, acc);
           VecIO<T, CW>::st(E + o, e);
         }
         const float rF = group_sum(pF, L.Lp2), rE = group_sum(pE, L.Lp2);
@@ -669,7 +728,7 @@ __global__ void __launch_bounds__(kBlock, PHIC_MIN_BLOCKS) recover_kernel(const 
           fmax_bits(mE, rE);
         }
       }
-      warp_parts(wp, mF, mE, bad, nf);
+      warp_parts(wp, mF, mE, 0, nf);
       cur ^= 1;
       if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, phase, wp); },
                           [&] {
@@ -775,25 +834,34 @@ cudaError_t coop_launch(K kernel, long long items, int max_per_sm, const SolveAr
   return cudaLaunchCooperativeKernel((const void*)kernel, dim3((unsigned)grid), dim3(kBlock), args, 0, st);
 }
 
-template <typename T>
-cudaError_t dispatch_series(const SolveArgs& a, cudaStream_t st, int* g) {
+template <typename T, int MINB>
+cudaError_t dispatch_series_b(const SolveArgs& a, cudaStream_t st, int* g) {
   const long long items = (long long)a.n * a.S_lay.Lp2;
   const int bps = blocks_per_sm(sizeof(T));
   switch (a.S_lay.cw) {
-    case 1: return coop_launch(series_kernel<T, 1>, items, bps, a, st, g);
-    case 2: return coop_launch(series_kernel<T, 2>, items, bps, a, st, g);
-    default: return coop_launch(series_kernel<T, 4>, items, bps, a, st, g);
+    case 1: return coop_launch(series_kernel<T, 1, MINB>, items, bps, a, st, g);
+    case 2: return coop_launch(series_kernel<T, 2, MINB>, items, bps, a, st, g);
+    default: return coop_launch(series_kernel<T, 4, MINB>, items, bps, a, st, g);
   }
 }
-template <typename T>
-cudaError_t dispatch_recover(const SolveArgs& a, cudaStream_t st, int* g) {
+template <typename T, int MINB>
+cudaError_t dispatch_recover_b(const SolveArgs& a, cudaStream_t st, int* g) {
   const long long items = (long long)a.n * a.F_lay.Lp2;
   const int bps = blocks_per_sm(sizeof(T));
   switch (a.F_lay.cw) {
-    case 1: return coop_launch(recover_kernel<T, 1>, items, bps, a, st, g);
-    case 2: return coop_launch(recover_kernel<T, 2>, items, bps, a, st, g);
-    default: return coop_launch(recover_kernel<T, 4>, items, bps, a, st, g);
+    case 1: return coop_launch(recover_kernel<T, 1, MINB>, items, bps, a, st, g);
+    case 2: return coop_launch(recover_kernel<T, 2, MINB>, items, bps, a, st, g);
+    default: return coop_launch(recover_kernel<T, 4, MINB>, items, bps, a, st, g);
   }
+}
+// Residency hint by tile width: 2 blocks per SM for tiles up to 4 columns, 3 for wider ones.
+template <typename T>
+cudaError_t dispatch_series(const SolveArgs& a, cudaStream_t st, int* g) {
+  return a.S_lay.w <= 4 ? dispatch_series_b<T, 2>(a, st, g) : dispatch_series_b<T, 3>(a, st, g);
+}
+template <typename T>
+cudaError_t dispatch_recover(const SolveArgs& a, cudaStream_t st, int* g) {
+  return a.F_lay.w <= 4 ? dispatch_recover_b<T, 2>(a, st, g) : dispatch_recover_b<T, 3>(a, st, g);
 }
 }  // namespace
 
