@@ -30,12 +30,32 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "φ-comb solves/s & SpMM HBM GB/s (% peak) at stated tol; p50/p99 serve latency"
-HS = (1e-4, 1e-2)
-TOL = 2.0**-53
-P, R = 3, 2
 # FP64 pipe of a GB300 SM: 2 FMA/clk (1.91 measured), 152 SMs, 2070 MHz maximum SM clock.
 FP64_PEAK_GOPS = 2.0 * 152 * 2.070
-WORKLOAD_NAME = "convdiff3d-64^3 Pe10 (n=262144) p=3 r=2 t=(h/2,h/3) alpha=(1/2,1/3) h={1e-4,1e-2} tol=2^-53"
+
+# Workload of the benchmark line (defaults) and the auxiliary FP32/FP64 precision workload.
+WORKLOADS = {
+    "convdiff3d-64": dict(hs=(1e-4, 1e-2), p=3, r=2, t=lambda h: [h / 2.0, h / 3.0],
+                          name="convdiff3d-64^3 Pe10 (n=262144) p=3 r=2 t=(h/2,h/3) alpha=(1/2,1/3) h={1e-4,1e-2}"),
+    "advdiff2d-1024": dict(hs=(1e-5, 1e-4), p=4, r=4, t=lambda h: [0.25 * h, 0.5 * h, 0.75 * h, h],
+                           name="advdiff2d-1024^2 Pe1e3 (n=1048576) p=4 r=4 t=(1/4,1/2,3/4,1)h alpha=1 h={1e-5,1e-4}"),
+}
+WORKLOAD = "convdiff3d-64"
+PRECISION = "f64"
+HS = WORKLOADS[WORKLOAD]["hs"]
+TOL = 2.0**-53
+P, R = 3, 2
+WORKLOAD_NAME = WORKLOADS[WORKLOAD]["name"] + " tol=2^-53"
+
+
+def configure(workload_name: str, precision: str):
+    """Select the workload and storage precision (f64: tol 2^-53; f32: tol 2^-24)."""
+    global WORKLOAD, PRECISION, HS, TOL, P, R, WORKLOAD_NAME
+    cfg = WORKLOADS[workload_name]
+    WORKLOAD, PRECISION = workload_name, precision
+    HS, P, R = cfg["hs"], cfg["p"], cfg["r"]
+    TOL = 2.0**-53 if precision == "f64" else 2.0**-24
+    WORKLOAD_NAME = cfg["name"] + (" tol=2^-53 FP64" if precision == "f64" else " tol=2^-24 FP32")
 
 
 def parse():
@@ -46,6 +66,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="convdiff3d-64", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
     ap.add_argument("--profile-solve", type=float, default=None, metavar="H",
                     help="profiler target: Algorithm 1 and two Algorithm 3 solves of the workload at step H, "
                          "no timing and no JSON line")
@@ -60,9 +82,9 @@ def profile_solve(h: float) -> int:
     from paper_2509_26475_gb300 import api
 
     A_h, V_h, alpha = workload()
-    A = api.DeviceCSR.from_host(A_h)
-    V = torch.as_tensor(V_h).cuda()
-    P = api.select_params(A, check=True)
+    A = api.DeviceCSR.from_host(A_h, dtype=torch_dtype())
+    V = torch.as_tensor(V_h).to(torch_dtype()).cuda()
+    P = api.select_params(A, tol=TOL, check=True)
     for _ in range(2):
         W, st = api.solve(A, V, t_of(h), alpha, TOL, P, check=True)
     print(api.read_stats(st))
@@ -76,12 +98,21 @@ def dist_env():
 def workload():
     from paper_2509_26475_gb300 import workloads as wl
 
-    w = wl.workload_convdiff3d_64(HS[0])
+    if WORKLOAD == "convdiff3d-64":
+        w = wl.workload_convdiff3d_64(HS[0])
+    else:
+        w = wl.workload_advdiff2d_1024(HS[0], TOL)
     return w["A"], w["V"], w["alpha"]
 
 
 def t_of(h):
-    return [h / 2.0, h / 3.0]
+    return WORKLOADS[WORKLOAD]["t"](h)
+
+
+def torch_dtype():
+    import torch
+
+    return torch.float64 if PRECISION == "f64" else torch.float32
 
 
 def recorded_traffic():
@@ -216,22 +247,24 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # Native run
 # ------------------------------------------------------------------------------------------------
-def recover_kernel_work(n, nnz, wf, p, r, terms, outer_steps):
+def recover_kernel_work(n, nnz, wf, p, r, terms, outer_steps, b=8):
     """Algorithmic FP64 operations and bytes of one recovery-kernel launch.
 
     Per Taylor term (n x wf block, wf = 2r): the product with A_1 = A - xi I (formed once per solve, as
     Algorithm 3 writes it) takes nnz multiply-adds per column, the column scale t_i/(s k) n,
     E <- E + F n, and the two infinity-norm row sums 2n operations per column: (nnz + 4n) wf.  Per
     recovery step the refresh E mu + S Jt costs (2 + p/2) n wf.  Bytes per term: CSR values and indices
-    (12 nnz + 4(n+1)) plus reading F, reading and writing E and writing the next F (4 n wf 8)."""
+    ((4 + b) nnz + 4(n+1)) plus reading F, reading and writing E and writing the next F (4 n wf b), with b
+    the bytes of a value (8 in FP64, 4 in FP32)."""
     ops = terms * (nnz + 4 * n) * wf + outer_steps * (2 + p / 2.0) * n * wf
-    bytes_ = terms * (12 * nnz + 4 * (n + 1) + 4 * n * wf * 8)
+    bytes_ = terms * ((4 + b) * nnz + 4 * (n + 1) + 4 * n * wf * b)
     return ops, bytes_
 
 
 def main():
     args = parse()
     rank, world, local_rank = dist_env()
+    configure(args.workload, args.precision)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.profile_solve is not None:
@@ -252,20 +285,22 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     A_h, V_h, alpha = workload()
-    A = api.DeviceCSR.from_host(A_h, device=dev)
-    V = torch.as_tensor(V_h).to(dev)
+    dt = torch_dtype()
+    prec = capi.PHIC_F64 if PRECISION == "f64" else capi.PHIC_F32
+    A = api.DeviceCSR.from_host(A_h, device=dev, dtype=dt)
+    V = torch.as_tensor(V_h).to(dt).to(dev)
     n, nnz = A.n, A.nnz
     params = api.new_params(dev)
     stats = [api.new_stats(dev) for _ in HS]
-    W = [torch.empty((R, n), dtype=torch.float64, device=dev) for _ in HS]
+    W = [torch.empty((R, n), dtype=dt, device=dev) for _ in HS]
     ws_sel = torch.empty(api.select_workspace_bytes(n), dtype=torch.uint8, device=dev)
-    ws_sol = torch.empty(api.solve_workspace_bytes(n, nnz, P, R, capi.PHIC_F64), dtype=torch.uint8, device=dev)
+    ws_sol = torch.empty(api.solve_workspace_bytes(n, nnz, P, R, prec), dtype=torch.uint8, device=dev)
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(ev_rec=None):
-        api.select_params(A, out=params, workspace=ws_sel)
+        api.select_params(A, tol=TOL, out=params, workspace=ws_sel)
         for idx, h in enumerate(HS):
             if ev_rec is not None and idx == len(HS) - 1:
                 api.solve(A, V, t_of(h), alpha, TOL, params, out=W[idx], stats=stats[idx], workspace=ws_sol,
@@ -316,7 +351,8 @@ def main():
     st_last = api.read_stats(stats[-1])
     prm = api.read_params(params)
     wf = 2 * R
-    ops, bytes_ = recover_kernel_work(n, nnz, wf, P, R, st_last["recovery_terms"], st_last["s_int"] - 1)
+    b = 8 if PRECISION == "f64" else 4
+    ops, bytes_ = recover_kernel_work(n, nnz, wf, P, R, st_last["recovery_terms"], st_last["s_int"] - 1, b)
     rec_s = statistics.mean(rec_ms) / 1000.0
     achieved = ops / rec_s / 1e9
     hbm_gbs = bytes_ / rec_s / 1e9
@@ -326,18 +362,27 @@ def main():
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    roofline = {"bound": "alu", "kernel": "recover_kernel (Algorithm 3 recovery loop, h=1e-2)",
-                "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
-                "frac": achieved / FP64_PEAK_GOPS, "traffic": recorded_traffic(),
-                "peak_note": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (probe measured 1.91 FMA/clk/SM)",
-                "launch_ms": statistics.mean(rec_ms), "terms_per_launch": st_last["recovery_terms"],
-                "hbm_view": {"algorithmic_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac_of_measured": hbm_gbs / hbm_peak,
-                             "note": "working set (~48 MB) is L2-resident inside a launch"}}
+    kernel = f"recover_kernel (Algorithm 3 recovery loop, h={HS[-1]:g})"
+    if PRECISION == "f64":
+        roofline = {"bound": "alu", "kernel": kernel,
+                    "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
+                    "frac": achieved / FP64_PEAK_GOPS,
+                    "traffic": recorded_traffic() if WORKLOAD == "convdiff3d-64" else None,
+                    "peak_note": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (probe measured 1.91 FMA/clk/SM)",
+                    "launch_ms": statistics.mean(rec_ms), "terms_per_launch": st_last["recovery_terms"],
+                    "hbm_view": {"algorithmic_gbs": hbm_gbs, "peak_gbs": hbm_peak,
+                                 "frac_of_measured": hbm_gbs / hbm_peak}}
+    else:
+        roofline = {"bound": "hbm", "kernel": kernel, "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_gbs / hbm_peak, "traffic": None,
+                    "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured)",
+                    "launch_ms": statistics.mean(rec_ms), "terms_per_launch": st_last["recovery_terms"]}
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "n": n, "nnz": nnz, "p": P, "r": R, "h": list(HS), "tol": "2^-53",
+            "vs_baseline": None, "dtype": PRECISION, "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "n": n, "nnz": nnz, "p": P, "r": R, "h": list(HS),
+                       "tol": "2^-53" if PRECISION == "f64" else "2^-24",
                        "step": "Algorithm 1 + Algorithm 3 at each h (2 solves)",
                        "l2": "flushed between steps (2 x L2 write, outside the step events)",
                        "parallelism": f"replicas x{world}",
@@ -350,7 +395,7 @@ def main():
 
     if not args.no_e2e:
         line["e2e"] = e2e(api, capi, A_h, V_h, alpha, dev, stream, K, world, dist)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD == "convdiff3d-64":
         times, cores = time_oracle(1, 0)
         line["cpu_baseline"] = {"value": len(HS) / times[0], "unit": "solves/s", "cores": cores, "kind": "oracle",
                                 "sample": "one full step (Algorithm 1 + Algorithm 3 at h=1e-4 and 1e-2) of the "
@@ -368,18 +413,19 @@ def e2e(api, capi, A_h, V_h, alpha, dev, stream, K, world, dist):
     import numpy as np
     import torch
 
+    dt = torch_dtype()
     rp = torch.as_tensor(A_h.rowptr).pin_memory()
     ci = torch.as_tensor(A_h.colidx).pin_memory()
-    va = torch.as_tensor(A_h.values).pin_memory()
-    Vp = torch.as_tensor(V_h).pin_memory()
-    outs = [torch.empty((R, A_h.n), dtype=torch.float64).pin_memory() for _ in HS]
-    h2d = rp.numel() * 4 + ci.numel() * 4 + va.numel() * 8 + Vp.numel() * 8
-    d2h = sum(o.numel() * 8 for o in outs)
+    va = torch.as_tensor(A_h.values).to(dt).pin_memory()
+    Vp = torch.as_tensor(V_h).to(dt).pin_memory()
+    outs = [torch.empty((R, A_h.n), dtype=dt).pin_memory() for _ in HS]
+    h2d = rp.numel() * 4 + ci.numel() * 4 + va.numel() * va.element_size() + Vp.numel() * Vp.element_size()
+    d2h = sum(o.numel() * o.element_size() for o in outs)
 
     def one():
         A = api.DeviceCSR(rp.to(dev, non_blocking=True), ci.to(dev, non_blocking=True), va.to(dev, non_blocking=True))
         V = Vp.to(dev, non_blocking=True)
-        Pm = api.select_params(A)
+        Pm = api.select_params(A, tol=TOL)
         for idx, h in enumerate(HS):
             Wd, _ = api.solve(A, V, t_of(h), alpha, TOL, Pm)
             outs[idx].copy_(Wd, non_blocking=True)

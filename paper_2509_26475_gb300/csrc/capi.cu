@@ -39,7 +39,7 @@ SelectLayout select_layout(int64_t n, int m) {
   L.ctl = 0;
   L.part = align_up(sizeof(Ctl));
   L.basis = L.part + align_up((size_t)2 * max_select_grid() * 16);
-  L.total = L.basis + align_up((size_t)n * (size_t)(m + 1) * sizeof(double));
+  L.total = L.basis + align_up((size_t)n * (size_t)((m + 2) / 2 * 2) * sizeof(double));  // pairs of vectors
   return L;
 }
 
@@ -50,8 +50,8 @@ struct SolveLayout {
 SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec) {
   SolveLayout L;
   const size_t es = prec == PHIC_F32 ? 4 : 8;
-  L.sl = pick_layout((p + 1) * r);
-  L.fl = pick_layout(p == 0 ? r : 2 * r);
+  L.sl = pick_layout((p + 1) * r, (int)es);
+  L.fl = pick_layout(p == 0 ? r : 2 * r, (int)es);
   const size_t tileS = align_up((size_t)n * L.sl.ws * es);
   const size_t tileF = align_up((size_t)n * L.fl.ws * es);
   size_t off = 0;

@@ -127,44 +127,57 @@ __device__ __forceinline__ double slot_get(const Ctl* c, int phase, int idx) {
 }
 
 // ---- scaled sum of squares: value = ssq * 2^(2e) ------------------------------------------------
+// The power-of-two scalings move the exponent field with integer operations (exact; on GB300 FP64
+// instructions are scarce), so adding an element costs one FP64 fused multiply-add.
 struct Ssq {
   int e;
   double ssq;
 };
 constexpr int kSsqEmpty = -4000;
+constexpr int kSsqNonfinite = 5000;
 
 __device__ __forceinline__ Ssq ssq_empty() { return Ssq{kSsqEmpty, 0.0}; }
 
+// x 2^-d for a finite normal x whose scaled exponent stays at most 1023; results under 2^-998 flush
+// to 0 (they lie at least 2^-998 below the running scale, so their squares cannot change the sum).
+__device__ __forceinline__ double pow2_down(double x, int d) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex - d <= 25) return 0.0;
+  return __longlong_as_double(b - (long long)d * 4503599627370496LL);  // d * 2^52
+}
+
 __device__ __forceinline__ void ssq_add(Ssq& a, double x) {
-  if (x == 0.0) return;
-  if (!isfinite(x)) {  // keep Inf/NaN visible
-    a.e = 5000;
+  const long long b = __double_as_longlong(x);
+  const int bex = (int)((b >> 52) & 0x7ff);
+  if (bex == 0) return;  // zero or subnormal: below 2^-1022, negligible against any normal element
+  if (bex == 0x7ff) {    // Inf or NaN: keep it visible
+    a.e = kSsqNonfinite;
     a.ssq = (double)NAN;
     return;
   }
-  if (a.e >= 5000) return;
-  int ex = ilogb(x);
-  if (ex < -1022) ex = -1022;
+  if (a.e >= kSsqNonfinite) return;
+  const int ex = bex - 1023;
   if (ex > a.e) {
-    a.ssq = (a.e == kSsqEmpty) ? 0.0 : scalbn(a.ssq, 2 * (a.e - ex));
+    a.ssq = (a.e == kSsqEmpty) ? 0.0 : pow2_down(a.ssq, 2 * (ex - a.e));
     a.e = ex;
   }
-  const double y = scalbn(x, -a.e);
+  const double y = pow2_down(x, a.e);  // x 2^-e, exponent at most 0
   a.ssq = fma(y, y, a.ssq);
 }
 
 __device__ __forceinline__ Ssq ssq_combine(Ssq a, Ssq b) {
   if (a.e == kSsqEmpty) return b;
   if (b.e == kSsqEmpty) return a;
-  if (a.e >= 5000 || b.e >= 5000) return Ssq{5000, (double)NAN};
+  if (a.e >= kSsqNonfinite || b.e >= kSsqNonfinite) return Ssq{kSsqNonfinite, (double)NAN};
   const int e = a.e > b.e ? a.e : b.e;
-  return Ssq{e, scalbn(a.ssq, 2 * (a.e - e)) + scalbn(b.ssq, 2 * (b.e - e))};
+  return Ssq{e, pow2_down(a.ssq, 2 * (e - a.e)) + pow2_down(b.ssq, 2 * (e - b.e))};
 }
 
 // log of the 2-norm; -inf for a zero vector, NaN when a non-finite value was seen.
 __device__ __forceinline__ double ssq_log_norm(Ssq a) {
   if (a.e == kSsqEmpty || a.ssq == 0.0) return -INFINITY;
-  if (a.e >= 5000) return (double)NAN;
+  if (a.e >= kSsqNonfinite) return (double)NAN;
   return (double)a.e * 0.69314718055994530942 + 0.5 * log(a.ssq);
 }
 

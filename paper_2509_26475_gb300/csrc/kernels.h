@@ -15,7 +15,7 @@ struct Ctl;
 struct TileLayout {
   int w, ws, cw, L, Lp2;
 };
-TileLayout pick_layout(int w);
+TileLayout pick_layout(int w, int elem_bytes);
 
 struct SolveState {
   int s_int;
@@ -80,7 +80,7 @@ struct SelectArgs {
   int m;
   double tol, delta;
   int max_evals;
-  double* Vb;    // basis, column k at Vb + k n
+  double* Vb;    // basis V_0..V_m, pair-interleaved: V_k[row] at ((k/2) n + row) 2 + k%2
   void* part;    // 2 x grid scaled sums of squares
   Ctl* ctl;
   phic_params* out;

@@ -124,22 +124,38 @@ __device__ __forceinline__ void put_partial(Ssq* part, int parity, Ssq blk) {
   if (threadIdx.x == 0) part[(size_t)parity * gridDim.x + blockIdx.x] = blk;
 }
 
-// Combines all blocks' partials in a fixed order; the result is valid in thread 0.
+// Combines all blocks' partials in a fixed order; the result is valid in thread 0.  Each lane of warp
+// 0 issues its loads (up to 8 at a time) before combining, so the L2 latencies overlap.
 __device__ Ssq gather_partials(const Ssq* part, int parity) {
   Ssq acc = ssq_empty();
   if (threadIdx.x < 32) {
     const volatile Ssq* pp = part + (size_t)parity * gridDim.x;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-      Ssq x;
-      x.e = pp[b].e;
-      x.ssq = pp[b].ssq;
-      acc = ssq_combine(acc, x);
+    for (int b0 = threadIdx.x; b0 < (int)gridDim.x; b0 += 32 * 8) {
+      Ssq x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = b0 + 32 * u;
+        x[u] = ssq_empty();
+        if (b < (int)gridDim.x) {
+          x[u].e = pp[b].e;
+          x[u].ssq = pp[b].ssq;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc = ssq_combine(acc, x[u]);
     }
     acc = warp_ssq(acc);
   }
   return acc;
 }
 
+// The basis is stored in interleaved pairs: V_k[row] at ((k/2) n + row) 2 + k%2, so that an objective
+// pass loads V_{2j} and V_{2j+1} of a row with one 16-byte load.
+__device__ __forceinline__ size_t vidx(int k, int n, long long row) {
+  return ((size_t)(k >> 1) * n + (size_t)row) * 2 + (k & 1);
+}
+
+// (A x)[row] for the basis vector x = V_k (pair-interleaved, stride 2).
 template <typename VT>
 __device__ __forceinline__ double spmv_row(const SelectArgs& a, const VT* __restrict__ vals, const double* x, int row,
                                            int& bad) {
@@ -148,7 +164,7 @@ __device__ __forceinline__ double spmv_row(const SelectArgs& a, const VT* __rest
   for (int q = beg; q < end; ++q) {
     const int col = __ldg(a.colidx + q);
     if ((unsigned)col >= (unsigned)a.n) { bad = 1; continue; }
-    acc = fma((double)__ldg(vals + q), x[col], acc);
+    acc = fma((double)__ldg(vals + q), x[(size_t)col * 2], acc);
   }
   return acc;
 }
@@ -191,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
         const double u = (double)(splitmix64_at(a.seed, (uint64_t)row) >> 11) * 0x1.0p-53;
         x = 2.0 * u - 1.0;
       }
-      V0[row] = x;
+      V0[vidx(0, n, row)] = x;
       ssq_add(acc, x);
     }
     const Ssq blk = block_ssq(acc);
@@ -220,8 +236,8 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
     Ssq acc = ssq_empty();
     const double nv = sh.nv;
     for (long long row = first; row < n; row += stride) {
-      const double x = V0[row] / nv;
-      V0[row] = x;
+      const double x = V0[vidx(0, n, row)] / nv;
+      V0[vidx(0, n, row)] = x;
       ssq_add(acc, x);
     }
     const Ssq blk = block_ssq(acc);
@@ -238,12 +254,11 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
   }
   // ---- guarded power basis ----------------------------------------------------------------------------
   for (int k = 1; k <= m && sh.go; ++k) {
-    const double* __restrict__ Vp = a.Vb + (size_t)(k - 1) * n;
-    double* __restrict__ Vk = a.Vb + (size_t)k * n;
+    const double* __restrict__ Vp = a.Vb + vidx(k - 1, n, 0);
     Ssq acc = ssq_empty();
     for (long long row = first; row < n; row += stride) {
       const double y = spmv_row<VT>(a, vals, Vp, (int)row, bad);
-      Vk[row] = y;
+      a.Vb[vidx(k, n, row)] = y;
       ssq_add(acc, y);
     }
     const Ssq blk = block_ssq(acc);
@@ -293,14 +308,14 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
   if (threadIdx.x >= 1 && threadIdx.x <= r) sh.coef[threadIdx.x] = exp(-(double)threadIdx.x * log(sh.s0));  // r <= 128 < kBlock
   __syncthreads();
   for (long long row = first; row < n; row += stride)
-    for (int j = 1; j <= r; ++j) a.Vb[(size_t)j * n + row] *= sh.coef[j];
+    for (int j = 1; j <= r; ++j) a.Vb[vidx(j, n, row)] *= sh.coef[j];
   if (!grid_sync(ctl, epoch, a.spin_ns)) return;
   // ---- extend: V_k = A V_{k-1} / s0, k = r+1..m -------------------------------------------------------
   for (int k = r + 1; k <= m; ++k) {
-    const double* __restrict__ Vp = a.Vb + (size_t)(k - 1) * n;
-    double* __restrict__ Vk = a.Vb + (size_t)k * n;
+    const double* __restrict__ Vp = a.Vb + vidx(k - 1, n, 0);
     const double inv_s0 = sh.inv_s0;
-    for (long long row = first; row < n; row += stride) Vk[row] = spmv_row<VT>(a, vals, Vp, (int)row, bad) * inv_s0;
+    for (long long row = first; row < n; row += stride)
+      a.Vb[vidx(k, n, row)] = spmv_row<VT>(a, vals, Vp, (int)row, bad) * inv_s0;
     if (!grid_sync(ctl, epoch, a.spin_ns)) return;
   }
   // ---- Brent on f(xi) ---------------------------------------------------------------------------------
@@ -331,9 +346,16 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
     }
     __syncthreads();
     Ssq acc = ssq_empty();
+    const double2* __restrict__ Vp2 = reinterpret_cast<const double2*>(a.Vb);
+    const int pairs = (m + 1) >> 1;
     for (long long row = first; row < n; row += stride) {
       double y = 0.0;
-      for (int kk = 0; kk <= m; ++kk) y = fma(sh.coef[kk], a.Vb[(size_t)kk * n + row], y);
+      for (int jj = 0; jj < pairs; ++jj) {  // y = sum_k coef_k V_k[row], k ascending
+        const double2 v = Vp2[(size_t)jj * n + row];
+        y = fma(sh.coef[2 * jj], v.x, y);
+        y = fma(sh.coef[2 * jj + 1], v.y, y);
+      }
+      if ((m + 1) & 1) y = fma(sh.coef[m], a.Vb[vidx(m, n, row)], y);
       ssq_add(acc, y);
     }
     const Ssq blk = block_ssq(acc);
@@ -387,8 +409,7 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t st, int* grid_out) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-  const int cap = blocks_per_sm(8);
-  if (per_sm > cap) per_sm = cap;
+  if (per_sm > 2) per_sm = 2;  // short passes: fewer blocks make the fixed-order combine and barrier cheaper
   long long need = ((long long)a.n + kBlock - 1) / kBlock;
   long long grid = (long long)sms * per_sm;
   if (need < grid) grid = need < 1 ? 1 : need;

@@ -38,6 +38,13 @@
 #ifndef PHIC_CW_MAX
 #define PHIC_CW_MAX 2
 #endif
+// FP32 tiles: widest column chunk (16 bytes = 4 floats) and rows in flight per thread.
+#ifndef PHIC_CW_MAX_F32
+#define PHIC_CW_MAX_F32 4
+#endif
+#ifndef PHIC_ROWS_F32
+#define PHIC_ROWS_F32 1
+#endif
 
 namespace phic {
 
@@ -118,12 +125,43 @@ __device__ __forceinline__ int scale_exponent(double ref) {
   return (ref > 0.0 && isfinite(ref)) ? ilogb(ref) : 0;
 }
 
-// acc[j] += sum_q B(row, col_q) X(col_q, c0 + j) over the row's stored entries, four at a time so that
+// Sum of products in the storage precision.  FP64: fused multiply-adds.  FP32: compensated (the
+// products' and sums' rounding errors are carried in a second FP32 word, error-free transformations
+// TwoProduct by FMA and TwoSum), so a row's sum is accurate to about one FP32 rounding whatever its
+// length; the FP32 path is memory-bound and these extra FP32 operations are free there.
+template <typename T>
+struct DotAcc {
+  T hi;
+  __device__ __forceinline__ void zero() { hi = T(0); }
+  __device__ __forceinline__ void add(T a, T x) { hi = fma(a, x, hi); }
+  __device__ __forceinline__ T value() const { return hi; }
+};
+template <>
+struct DotAcc<float> {
+  float hi, lo;
+  __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+  // explicitly rounded operations: a contraction into an FMA would break the error-free transformations
+  __device__ __forceinline__ void add(float a, float x) {
+    const float p = __fmul_rn(a, x);
+    const float pe = fmaf(a, x, -p);  // exact error of the product
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));  // exact error of the sum
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(pe, se));
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(hi, lo); }
+};
+
+// acc[j] = sum_q B(row, col_q) X(col_q, c0 + j) over the row's stored entries, four at a time so that
 // their gathers are in flight together.  Columns were checked when the entries were written.
 template <typename T, int CW>
 __device__ __forceinline__ void spmm_ent(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent,
                                          const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW]) {
   const int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
+  DotAcc<T> d[CW];
+#pragma unroll
+  for (int j = 0; j < CW; ++j) d[j].zero();
   for (int q0 = beg; q0 < end; q0 += 4) {
     const int cnt = end - q0;
     CsrEnt<T> e[4];
@@ -138,9 +176,60 @@ __device__ __forceinline__ void spmm_ent(const int* __restrict__ rowptr, const C
     for (int u = 0; u < 4; ++u)
       if (u < cnt) {
 #pragma unroll
-        for (int j = 0; j < CW; ++j) acc[j] = fma(e[u].v, x[u][j], acc[j]);
+        for (int j = 0; j < CW; ++j) d[j].add(e[u].v, x[u][j]);
       }
   }
+#pragma unroll
+  for (int j = 0; j < CW; ++j) acc[j] = d[j].value();
+}
+
+// The same for NR rows at once: their row bounds, entries and gathers are all issued before any is
+// used, so NR dependent load chains (row bounds -> entries -> gathers) overlap in one thread.  The FP32
+// path is bound by memory latency, not by FP64 issue, and takes NR = 4.
+template <typename T, int CW, int NR>
+__device__ __forceinline__ void spmm_rows(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent,
+                                          const T* __restrict__ X, int ws, int c0, const int (&row)[NR],
+                                          const bool (&act)[NR], T (&acc)[NR][CW]) {
+  int beg[NR], cnt[NR];
+#pragma unroll
+  for (int u = 0; u < NR; ++u) {
+    beg[u] = act[u] ? __ldg(rowptr + row[u]) : 0;
+    cnt[u] = act[u] ? __ldg(rowptr + row[u] + 1) - beg[u] : 0;
+  }
+  int mx = 0;
+#pragma unroll
+  for (int u = 0; u < NR; ++u) mx = cnt[u] > mx ? cnt[u] : mx;
+  DotAcc<T> d[NR][CW];
+#pragma unroll
+  for (int u = 0; u < NR; ++u)
+#pragma unroll
+    for (int j = 0; j < CW; ++j) d[u][j].zero();
+  for (int q0 = 0; q0 < mx; q0 += 4) {
+    CsrEnt<T> e[NR][4];
+#pragma unroll
+    for (int u = 0; u < NR; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (q0 + v < cnt[u]) e[u][v] = ent[beg[u] + q0 + v];
+    T x[NR][4][CW];
+#pragma unroll
+    for (int u = 0; u < NR; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (q0 + v < cnt[u]) VecIO<T, CW>::ld(X + (size_t)e[u][v].col * ws + c0, x[u][v]);
+#pragma unroll
+    for (int u = 0; u < NR; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (q0 + v < cnt[u]) {
+#pragma unroll
+          for (int j = 0; j < CW; ++j) d[u][j].add(e[u][v].v, x[u][v][j]);
+        }
+  }
+#pragma unroll
+  for (int u = 0; u < NR; ++u)
+#pragma unroll
+    for (int j = 0; j < CW; ++j) acc[u][j] = d[u][j].value();
 }
 
 // |x| 2^-e0 as an FP32 value, for the infinity-norm sums that feed the truncation test.  For a double
@@ -687,45 +776,59 @@ __global__ void __launch_bounds__(kBlock, MINB) recover_kernel(const SolveArgs a
       const int bias = lc.bias;
       const float fscale = lc.fscale;
       int nf = 0;
-      for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
-        const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
-        const bool act = row < br.r1 && lane < L.L;
-        float pF = 0.f, pE = 0.f;
-        if (act) {
-          const size_t o = (size_t)row * L.ws + c0;
-          T acc[CW];
+      constexpr int NR = sizeof(T) == 4 ? PHIC_ROWS_F32 : 1;  // rows in flight per thread
+      const int lane = threadIdx.x & lmask;
+      for (long long it0 = threadIdx.x; it0 < br.padded; it0 += (long long)NR * kBlock) {
+        int row[NR];
+        bool act[NR];
 #pragma unroll
-          for (int j = 0; j < CW; ++j) acc[j] = T(0);
-          spmm_ent<T, CW>(a.rowptr, ent, Go, L.ws, c0, row, acc);
-          const bool shift_row = nodiag && a.rowflag[row];
-          T e[CW];
-          if (kk == 1 || shift_row) {
-            T own[CW];
-            VecIO<T, CW>::ld(Go + o, own);
-            if (shift_row) {
-#pragma unroll
-              for (int j = 0; j < CW; ++j) acc[j] = fma(xiB, own[j], acc[j]);
-            }
-            if (kk == 1) {
-#pragma unroll
-              for (int j = 0; j < CW; ++j) e[j] = own[j];  // E = F at the start of the step
-            }
-          }
-          if (kk != 1) VecIO<T, CW>::ld(E + o, e);
-#pragma unroll
-          for (int j = 0; j < CW; ++j) {
-            // F_k = c_k G_k;  E <- E + F_k
-            e[j] = fma(kC[j], acc[j], e[j]);
-            pF += kF[j] * norm_piece(acc[j], bias, fscale, nf);
-            pE += norm_piece(e[j], bias, fscale, nf);
-          }
-          VecIO<T, CW>::st(Gn + o, acc);
-          VecIO<T, CW>::st(E + o, e);
+        for (int u = 0; u < NR; ++u) {
+          const long long it = it0 + (long long)u * kBlock;
+          row[u] = br.r0 + (int)(it >> br.shift);
+          act[u] = it < br.padded && row[u] < br.r1 && lane < L.L;
         }
-        const float rF = group_sum(pF, L.Lp2), rE = group_sum(pE, L.Lp2);
-        if (act && lane == 0) {
-          fmax_bits(mF, rF);
-          fmax_bits(mE, rE);
+        T acc[NR][CW];
+        spmm_rows<T, CW, NR>(a.rowptr, ent, Go, L.ws, c0, row, act, acc);
+        float pF[NR], pE[NR];
+#pragma unroll
+        for (int u = 0; u < NR; ++u) {
+          pF[u] = 0.f;
+          pE[u] = 0.f;
+          if (act[u]) {
+            const size_t o = (size_t)row[u] * L.ws + c0;
+            const bool shift_row = nodiag && a.rowflag[row[u]];
+            T e[CW];
+            if (kk == 1 || shift_row) {
+              T own[CW];
+              VecIO<T, CW>::ld(Go + o, own);
+              if (shift_row) {
+#pragma unroll
+                for (int j = 0; j < CW; ++j) acc[u][j] = fma(xiB, own[j], acc[u][j]);
+              }
+              if (kk == 1) {
+#pragma unroll
+                for (int j = 0; j < CW; ++j) e[j] = own[j];  // E = F at the start of the step
+              }
+            }
+            if (kk != 1) VecIO<T, CW>::ld(E + o, e);
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+              // F_k = c_k G_k;  E <- E + F_k
+              e[j] = fma(kC[j], acc[u][j], e[j]);
+              pF[u] += kF[j] * norm_piece(acc[u][j], bias, fscale, nf);
+              pE[u] += norm_piece(e[j], bias, fscale, nf);
+            }
+            VecIO<T, CW>::st(Gn + o, acc[u]);
+            VecIO<T, CW>::st(E + o, e);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < NR; ++u) {
+          const float rF = group_sum(pF[u], L.Lp2), rE = group_sum(pE[u], L.Lp2);
+          if (act[u] && lane == 0) {
+            fmax_bits(mF, rF);
+            fmax_bits(mE, rE);
+          }
         }
       }
       warp_parts(wp, mF, mE, 0, nf);
@@ -872,13 +975,14 @@ cudaError_t launch_recover(const SolveArgs& a, int prec, cudaStream_t st, int* g
   return prec == PHIC_F32 ? dispatch_recover<float>(a, st, grid_out) : dispatch_recover<double>(a, st, grid_out);
 }
 
-TileLayout pick_layout(int w) {
+TileLayout pick_layout(int w, int elem_bytes) {
+  const int cw_max = elem_bytes == 4 ? PHIC_CW_MAX_F32 : PHIC_CW_MAX;
   TileLayout t;
   t.w = w;
-  if (PHIC_CW_MAX >= 4 && w % 4 == 0 && w / 4 <= 32) {
+  if (cw_max >= 4 && w % 4 == 0 && w / 4 <= 32) {
     t.cw = 4;
     t.ws = w;
-  } else if (PHIC_CW_MAX >= 2 && w % 2 == 0 && w / 2 <= 32) {
+  } else if (cw_max >= 2 && w % 2 == 0 && w / 2 <= 32) {
     t.cw = 2;
     t.ws = w;
   } else if (w <= 32) {

@@ -163,3 +163,22 @@ def test_convdiff3d_64_full_size(oracle_mod):
         sel = oracle_mod.select(w["A"]) if h == 1e-4 else sel
         errs, gst, ost = _check_parity(oracle_mod, w["A"], w["V"], w["t"], w["alpha"], s=sel["s"], xi=sel["xi"])
         print(f"h={h}: errs={errs} gpu={gst} oracle={ost}")
+
+
+def test_advdiff2d_1024_full_size_fp64_and_fp32(oracle_mod):
+    """The precision workload at full size (n = 1,048,576, Peclet 1e3, p = 4, r = 4, h = 1e-5), compared
+    whole: FP64 at tol 2^-53 within 1e-12 and FP32 at tol 2^-24 within 5e-6 of the FP64 oracle."""
+    oracle_mod.set_threads(0)
+    w = wl.workload_advdiff2d_1024(1e-5, 2.0**-53)
+    sel = oracle_mod.select(w["A"])
+    ref, ost = oracle_mod.solve(w["A"], w["V"], w["t"], w["alpha"], TOL53, sel["s"], sel["xi"])
+    W, gst = _gpu_solve(w["A"], w["V"], w["t"], w["alpha"], TOL53, sel["s"], sel["xi"])
+    assert gst["status"] == 0 and gst["s_int"] == ost["s_int"] > 1
+    assert max(_rel(W, ref)) <= 1e-12
+    # FP32 with the parameters Algorithm 1 picks for tol = 2^-24; the exact result does not depend on
+    # (s, xi), so the FP64 oracle result above is the reference
+    sel24 = oracle_mod.select(w["A"], tol=TOL24)
+    W32, g32 = _gpu_solve(w["A"], w["V"], w["t"], w["alpha"], TOL24, sel24["s"], sel24["xi"], dtype=torch.float32)
+    assert g32["status"] == 0
+    assert max(_rel(W32, ref)) <= 5e-6
+    print(f"advdiff 1024^2 h=1e-5: fp64 errs={_rel(W, ref)} fp32 errs={_rel(W32, ref)} s_int={gst['s_int']}")
