@@ -13,7 +13,7 @@ constexpr int kBlock = 256;  // threads per block of every persistent kernel
 
 // Control block at the head of each persistent kernel's workspace region; zeroed before launch.
 struct __align__(256) Ctl {
-  unsigned long long bar;  // grid-barrier arrivals since launch (monotone: epoch e completes at e * gridDim.x)
+  unsigned long long bar;  // team-barrier arrivals since launch (monotone: epoch e completes at e * team size)
   int status;              // first phic_status != OK seen by any block
   int fault;               // unused padding kept for layout stability
   unsigned long long slot[4][4];  // max-reduction slots (bit patterns of non-negative values), by phase % 4
@@ -40,34 +40,47 @@ __device__ __forceinline__ unsigned long long bar_load(const unsigned long long*
   return v;
 }
 
-// Grid-wide barrier of a cooperative launch with leader work on both sides.  Every thread of every
-// block calls it; `epoch` (kept by thread 0 of each block) counts the barriers this block has passed.
-// Thread 0 runs pre() after its block's threads have arrived (their writes are visible to it) and before
-// it signals arrival with a release reduction on the monotone counter; it then polls the counter with
-// acquire loads until every block has arrived (epoch * gridDim.x arrivals), runs post() (reads the grid
-// results, decides, writes shared memory) and releases the block.  The release/acquire pair orders
-// every write made before the barrier by any thread of the grid before every read after it.  A wait
-// longer than spin_ns sets PHIC_TIMEOUT and returns false in every thread of the block that gave up;
-// the caller then leaves the kernel, so no block ever waits without bound.
+// The CTAs that work on one problem instance together: the whole grid of a single-instance launch, or
+// a subset of a batched launch.  `rank` and `size` replace blockIdx.x and gridDim.x inside the method's
+// kernels; `ctl` is the instance's control block (zeroed before the launch); thread 0 of each member keeps
+// `epoch`, the number of team barriers it has passed in this launch.
+struct Team {
+  Ctl* ctl;
+  int rank, size;
+  unsigned long long spin_ns;
+  unsigned long long epoch;
+};
+
+__device__ __forceinline__ Team grid_team(Ctl* c, unsigned long long spin_ns) {
+  return Team{c, (int)blockIdx.x, (int)gridDim.x, spin_ns, 0ull};
+}
+
+// Team barrier with leader work on both sides.  Every thread of every member calls it.  Thread 0 runs
+// pre() after its block's threads have arrived (their writes are visible to it) and before it signals
+// arrival with a release reduction on the monotone counter; it then polls the counter with acquire loads
+// until every member has arrived (epoch * size arrivals), runs post() (reads the team's results, decides,
+// writes shared memory) and releases the block.  The release/acquire pair orders every write made
+// before the barrier by any thread of the team before every read after it.  A wait longer than spin_ns
+// sets PHIC_TIMEOUT and returns false in every thread of the block that gave up; the caller then leaves
+// the instance, so no block ever waits without bound.
 template <typename Pre, typename Post>
-__device__ __forceinline__ bool grid_sync_lead(Ctl* c, unsigned long long& epoch, unsigned long long spin_ns,
-                                               Pre&& pre, Post&& post) {
+__device__ __forceinline__ bool team_sync_lead(Team& tm, Pre&& pre, Post&& post) {
   __shared__ int s_ok2;
   __syncthreads();
   if (threadIdx.x == 0) {
     pre();
     int ok = 1;
-    epoch += 1;
-    if (gridDim.x > 1) {
-      const unsigned long long target = epoch * gridDim.x;
-      bar_arrive(&c->bar);
-      if (bar_load(&c->bar) < target) {
+    tm.epoch += 1;
+    if (tm.size > 1) {
+      const unsigned long long target = tm.epoch * (unsigned long long)tm.size;
+      bar_arrive(&tm.ctl->bar);
+      if (bar_load(&tm.ctl->bar) < target) {
         const unsigned long long t0 = global_ns();
         unsigned spins = 0;
-        while (bar_load(&c->bar) < target) {
-          if ((++spins & 31u) == 0 && global_ns() - t0 > spin_ns) {
+        while (bar_load(&tm.ctl->bar) < target) {
+          if ((++spins & 31u) == 0 && global_ns() - t0 > tm.spin_ns) {
             ok = 0;
-            set_status(c, PHIC_TIMEOUT);
+            set_status(tm.ctl, PHIC_TIMEOUT);
             break;
           }
         }
@@ -82,8 +95,8 @@ __device__ __forceinline__ bool grid_sync_lead(Ctl* c, unsigned long long& epoch
   return s_ok2 != 0;
 }
 
-__device__ __forceinline__ bool grid_sync(Ctl* c, unsigned long long& epoch, unsigned long long spin_ns) {
-  return grid_sync_lead(c, epoch, spin_ns, [] {}, [] {});
+__device__ __forceinline__ bool team_sync(Team& tm) {
+  return team_sync_lead(tm, [] {}, [] {});
 }
 
 // ---- max over the grid of non-negative doubles, carried as their bit patterns --------------------
@@ -116,8 +129,10 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
   return v;
 }
 
-__device__ __forceinline__ void slot_reset(Ctl* c, int phase) {
-  if (blockIdx.x == 0 && threadIdx.x < 4) c->slot[(phase + 2) & 3][threadIdx.x] = 0ull;
+// Slots of phase p + 2 are cleared by the team's rank 0 during phase p (every member has read them in
+// phase p - 2 before arriving at barrier p - 1, and writes them only after barrier p + 1).
+__device__ __forceinline__ void slot_reset(const Team& tm, int phase) {
+  if (tm.rank == 0 && threadIdx.x < 4) tm.ctl->slot[(phase + 2) & 3][threadIdx.x] = 0ull;
 }
 __device__ __forceinline__ void slot_max(Ctl* c, int phase, int idx, unsigned long long v) {
   atomicMax(&c->slot[phase & 3][idx], v);

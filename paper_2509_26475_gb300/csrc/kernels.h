@@ -17,6 +17,8 @@ struct TileLayout {
 };
 TileLayout pick_layout(int w, int elem_bytes);
 
+// Per-solve loop state in device memory.  The series writes the first block; the recovery reads it and,
+// when it stops between outer steps (a bounded slice of a batched launch), records where to resume.
 struct SolveState {
   int s_int;
   int series_terms;
@@ -24,7 +26,14 @@ struct SolveState {
   int nodiag;  // some row stores no diagonal entry (its shift is applied explicitly)
   double xi;
   double s;
-  double pad2[4];
+  int status;     // outcome of the series (PHIC_OK: the recovery may run)
+  int rec_init;   // 1 once the first block F has been formed
+  int j_done;     // recovery outer steps completed
+  int cur;        // Ft buffer that holds F
+  double cF;      // ||F||_inf after the last refresh
+  long long rec_terms;
+  int max_inner;
+  int done;       // 1 once the output has been written
 };
 
 // Entry of the solve's copy of A_1 = A - xi I, scaled by 2^-eA: column and value in one aligned load.
@@ -87,6 +96,33 @@ struct SelectArgs {
   unsigned long long spin_ns;
 };
 
+// One instance of a batched launch: its solve and selection arguments (both pointing at the instance's
+// control block for this launch) and the phases to run.
+constexpr int kPhaseSelect = 1, kPhaseSeries = 2, kPhaseRecover = 4;
+struct BatchInst {
+  SolveArgs sa;
+  SelectArgs sel;
+  int phases;     // kPhase* bits
+  int team;       // CTAs that run this instance together
+  int prec;       // PHIC_F64 or PHIC_F32
+  int max_steps;  // recovery outer steps in this launch (a slice); INT_MAX: to the end
+};
+
+// Schedule entry: the instance a CTA works on next and its rank in that instance's team.  Every CTA's
+// entries follow one global order of the instances, so with all CTAs resident no team waits on a CTA
+// that waits on it.
+struct SchedEntry {
+  int inst;
+  int rank;
+};
+
+struct BatchArgs {
+  const BatchInst* inst;
+  const int* sched_ptr;     // [grid + 1]: entries of CTA b are sched[sched_ptr[b] .. sched_ptr[b+1])
+  const SchedEntry* sched;
+  unsigned long long spin_ns;
+};
+
 // Each returns a cudaError_t of the cooperative launch (or of the attribute queries).
 cudaError_t launch_series(const SolveArgs& a, int prec, cudaStream_t st, int* grid_out);
 cudaError_t launch_recover(const SolveArgs& a, int prec, cudaStream_t st, int* grid_out);
@@ -95,5 +131,9 @@ cudaError_t launch_params_set(phic_params* p, double xi, double s, cudaStream_t 
 int max_select_grid();
 void count_launch();
 int blocks_per_sm(int elem_bytes);
+// Batched launch with `grid` CTAs of the kernel built for `minb` (2 or 3) resident blocks per SM.
+cudaError_t launch_batch(const BatchArgs& b, int grid, int minb, cudaStream_t st);
+// Resident blocks per SM of the batched kernel built for minb (0 on error).
+int batch_occupancy(int minb);
 
 }  // namespace phic

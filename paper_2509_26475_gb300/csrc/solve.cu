@@ -1,914 +1,22 @@
-// Algorithm 3 of the paper (Section 4): block scaling-and-recovering truncated Taylor method for
-// w_i = sum_j alpha_i^j phi_j(t_i A) v_j, i = 1..r.
-//
-// Two persistent cooperative kernels share one workspace:
-//   series_kernel   -- setup (A_1 = A - xi I formed once, the reordered and scaled V), then the block
-//                      series S = sum_k D_k / k! of Theorem 1 (eq. rec.D with the shift of
-//                      eq. cD.shift), term by term with the truncation test (3.3).
-//   recover_kernel  -- the first-block recovery F(:,1:r) <- A F(:,1:r) T + v0 1^T, the s-1 recovery
-//                      steps of eq. rec.F.shift (Taylor series of exp(A_1 T/s) with the same test, the
-//                      undo factor mu and the refresh from S), and the output w_i = F_i + alpha_i F_{r+i}.
-// The data-dependent loops never return to the host: every Taylor term ends at a bounded grid barrier
-// inside which thread 0 of every block reads the same grid-wide norms, takes the same branch and
-// publishes it to its block.
-//
-// Work split: block b owns the contiguous rows [b n / G, (b+1) n / G) in every pass (balanced to one
-// row).  Tiles are row-major: row i of an n x w block is w consecutive values at row stride ws (see
-// pick_layout).  Each row is processed by L lanes of CW columns; the lanes of a row are consecutive in
-// a warp, so the row sums of |x| for the infinity norm are shuffle reductions.  A thread keeps the
-// same lane in every pass, so its per-column constants live in registers.
-//
-// GB300 cost model.  FP64 arithmetic runs at 2 FMA/clk/SM and shares its issue path with the load,
-// store and shuffle instructions (one memory instruction costs about 1.25 FP64 FMA there, integer
-// and FP32 work cost nothing there).  Hence:
-//   - the operator is held as B = (A - xi I) 2^-eA in (column, value) pairs, one 16-byte load per
-//     nonzero, with ||B||_inf < 1 (2^-eA is an exact scaling);
-//   - the recovery carries G_k = B^k F_0 unscaled and F_k = c_k G_k with per-column FP64 scalars
-//     c_k = (t_i 2^eA / s)^k / k! kept by thread 0, so E <- E + F_k is one FMA per element;
-//   - the infinity norms that decide when a Taylor loop stops are summed in FP32 from the high words
-//     of the doubles (norm_piece), with no FP64 instruction.
-#include <math.h>
-
-#include "common.cuh"
-#include "kernels.h"
-
-// Tile shape of the block kernels: widest column chunk a lane takes (1, 2 or 4).  Two columns per lane
-// with two (narrow tiles) or three (tiles of 8 or more columns) resident blocks per SM measured fastest
-// on GB300 for FP64: more warps hide the gathers, and wider chunks need registers that cost residency.
-#ifndef PHIC_CW_MAX
-#define PHIC_CW_MAX 2
-#endif
-// FP32 tiles: widest column chunk (16 bytes = 4 floats) and rows in flight per thread.
-#ifndef PHIC_CW_MAX_F32
-#define PHIC_CW_MAX_F32 4
-#endif
-#ifndef PHIC_ROWS_F32
-#define PHIC_ROWS_F32 1
-#endif
+// Single-instance launches of Algorithm 3: one cooperative grid per phase, the whole grid one team.
+#include "solve_body.cuh"
 
 namespace phic {
 
-namespace {
-
-// Contiguous rows of this block and the walk over their (row, lane) items in steps of the block size
-// (uniform within the block, so the shuffles always see full warps).
-struct BlockRows {
-  int r0, r1;
-  int shift;         // log2(Lp2)
-  long long padded;  // (r1 - r0) * Lp2 rounded up to a multiple of the block size
-  __device__ BlockRows(int n, int Lp2) {
-    r0 = (int)((long long)blockIdx.x * n / gridDim.x);
-    r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
-    shift = __ffs(Lp2) - 1;
-    const long long items = (long long)(r1 - r0) << shift;
-    padded = (items + kBlock - 1) / kBlock * kBlock;
-  }
-};
-
-__device__ __forceinline__ void umax(unsigned long long& m, double v) {
-  const unsigned long long u = dbits(v);
-  m = u > m ? u : m;
-}
-
-// Per-warp maxima of two values and the bad-index / non-finite flags; thread 0 folds them into the
-// grid slots inside the barrier.
-struct WarpParts {
-  unsigned long long a[kBlock / 32], b[kBlock / 32];
-  int bad[kBlock / 32], nonfinite[kBlock / 32];
-};
-
-__device__ __forceinline__ void warp_parts(WarpParts& wp, unsigned long long a, unsigned long long b, int bad,
-                                           int nonfinite = 0) {
-  a = warp_max_u64(a);
-  b = warp_max_u64(b);
-  const int anyb = __any_sync(0xffffffffu, bad);
-  const int anyn = __any_sync(0xffffffffu, nonfinite);
-  if ((threadIdx.x & 31) == 0) {
-    wp.a[threadIdx.x >> 5] = a;
-    wp.b[threadIdx.x >> 5] = b;
-    wp.bad[threadIdx.x >> 5] = anyb;
-    wp.nonfinite[threadIdx.x >> 5] = anyn;
-  }
-}
-
-// Slot 2 collects the non-finite flag of a pass (as 0/1).
-__device__ __forceinline__ void parts_to_slots(Ctl* c, int phase, const WarpParts& wp) {
-  unsigned long long a = 0, b = 0;
-  int bad = 0, nf = 0;
-  for (int w = 0; w < kBlock / 32; ++w) {
-    a = wp.a[w] > a ? wp.a[w] : a;
-    b = wp.b[w] > b ? wp.b[w] : b;
-    bad |= wp.bad[w];
-    nf |= wp.nonfinite[w];
-  }
-  slot_max(c, phase, 0, a);
-  slot_max(c, phase, 1, b);
-  if (nf) slot_max(c, phase, 2, 1ull);
-  if (bad) set_status(c, PHIC_INVALID_ARG);
-}
-
-// Grid-wide norm published in a slot by the float path, back to FP64 (scaled by 2^e0).
-__device__ __forceinline__ double slot_norm(const Ctl* c, int phase, int idx, int e0) {
-  const unsigned long long u = *(volatile const unsigned long long*)&c->slot[phase & 3][idx];
-  return ldexp((double)__int_as_float((int)(unsigned)u), e0);
-}
-__device__ __forceinline__ bool slot_nonfinite(const Ctl* c, int phase) {
-  return *(volatile const unsigned long long*)&c->slot[phase & 3][2] != 0ull;
-}
-__device__ __forceinline__ void fmax_bits(unsigned long long& m, float v) {
-  const unsigned long long u = (unsigned)__float_as_int(v);
-  m = u > m ? u : m;
-}
-// bias of norm_piece for the scale 2^-e0
-__device__ __forceinline__ int norm_bias(int e0) { return (896 + e0) << 20; }
-__device__ __forceinline__ int scale_exponent(double ref) {
-  return (ref > 0.0 && isfinite(ref)) ? ilogb(ref) : 0;
-}
-
-// Sum of products in the storage precision.  FP64: fused multiply-adds.  FP32: compensated (the
-// products' and sums' rounding errors are carried in a second FP32 word, error-free transformations
-// TwoProduct by FMA and TwoSum), so a row's sum is accurate to about one FP32 rounding whatever its
-// length; the FP32 path is memory-bound and these extra FP32 operations are free there.
-template <typename T>
-struct DotAcc {
-  T hi;
-  __device__ __forceinline__ void zero() { hi = T(0); }
-  __device__ __forceinline__ void add(T a, T x) { hi = fma(a, x, hi); }
-  __device__ __forceinline__ T value() const { return hi; }
-};
-template <>
-struct DotAcc<float> {
-  float hi, lo;
-  __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
-  // explicitly rounded operations: a contraction into an FMA would break the error-free transformations
-  __device__ __forceinline__ void add(float a, float x) {
-    const float p = __fmul_rn(a, x);
-    const float pe = fmaf(a, x, -p);  // exact error of the product
-    const float s = __fadd_rn(hi, p);
-    const float bb = __fsub_rn(s, hi);
-    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));  // exact error of the sum
-    hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(pe, se));
-  }
-  __device__ __forceinline__ float value() const { return __fadd_rn(hi, lo); }
-};
-
-// acc[j] = sum_q B(row, col_q) X(col_q, c0 + j) over the row's stored entries, four at a time so that
-// their gathers are in flight together.  Columns were checked when the entries were written.
-template <typename T, int CW>
-__device__ __forceinline__ void spmm_ent(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent,
-                                         const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW]) {
-  const int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
-  DotAcc<T> d[CW];
-#pragma unroll
-  for (int j = 0; j < CW; ++j) d[j].zero();
-  for (int q0 = beg; q0 < end; q0 += 4) {
-    const int cnt = end - q0;
-    CsrEnt<T> e[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (u < cnt) e[u] = ent[q0 + u];
-    T x[4][CW];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (u < cnt) VecIO<T, CW>::ld(X + (size_t)e[u].col * ws + c0, x[u]);
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (u < cnt) {
-#pragma unroll
-        for (int j = 0; j < CW; ++j) d[j].add(e[u].v, x[u][j]);
-      }
-  }
-#pragma unroll
-  for (int j = 0; j < CW; ++j) acc[j] = d[j].value();
-}
-
-// The same for NR rows at once: their row bounds, entries and gathers are all issued before any is
-// used, so NR dependent load chains (row bounds -> entries -> gathers) overlap in one thread.  The FP32
-// path is bound by memory latency, not by FP64 issue, and takes NR = 4.
-template <typename T, int CW, int NR>
-__device__ __forceinline__ void spmm_rows(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent,
-                                          const T* __restrict__ X, int ws, int c0, const int (&row)[NR],
-                                          const bool (&act)[NR], T (&acc)[NR][CW]) {
-  int beg[NR], cnt[NR];
-#pragma unroll
-  for (int u = 0; u < NR; ++u) {
-    beg[u] = act[u] ? __ldg(rowptr + row[u]) : 0;
-    cnt[u] = act[u] ? __ldg(rowptr + row[u] + 1) - beg[u] : 0;
-  }
-  int mx = 0;
-#pragma unroll
-  for (int u = 0; u < NR; ++u) mx = cnt[u] > mx ? cnt[u] : mx;
-  DotAcc<T> d[NR][CW];
-#pragma unroll
-  for (int u = 0; u < NR; ++u)
-#pragma unroll
-    for (int j = 0; j < CW; ++j) d[u][j].zero();
-  for (int q0 = 0; q0 < mx; q0 += 4) {
-    CsrEnt<T> e[NR][4];
-#pragma unroll
-    for (int u = 0; u < NR; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (q0 + v < cnt[u]) e[u][v] = ent[beg[u] + q0 + v];
-    T x[NR][4][CW];
-#pragma unroll
-    for (int u = 0; u < NR; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (q0 + v < cnt[u]) VecIO<T, CW>::ld(X + (size_t)e[u][v].col * ws + c0, x[u][v]);
-#pragma unroll
-    for (int u = 0; u < NR; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (q0 + v < cnt[u]) {
-#pragma unroll
-          for (int j = 0; j < CW; ++j) d[u][j].add(e[u][v].v, x[u][v][j]);
-        }
-  }
-#pragma unroll
-  for (int u = 0; u < NR; ++u)
-#pragma unroll
-    for (int j = 0; j < CW; ++j) acc[u][j] = d[u][j].value();
-}
-
-// |x| 2^-e0 as an FP32 value, for the infinity-norm sums that feed the truncation test.  For a double
-// the high word (sign, exponent, 20 mantissa bits) is rebiased into FP32 layout with integer
-// operations (relative truncation below 2^-20; values under 2^-126 of the scale flush to 0, values above
-// 2^128 saturate) so that the norms cost no FP64 instruction; Inf and NaN raise `nonfinite`.  bias
-// carries (896 + e0) << 20.  An FP32 element is scaled exactly.
-__device__ __forceinline__ float norm_piece(double x, int bias, float scale, int& nonfinite) {
-  (void)scale;
-  const int h = __double2hiint(x) & 0x7fffffff;
-  nonfinite |= h >= 0x7ff00000;
-  int t = h - bias;
-  t = t < 0 ? 0 : t;
-  t = t > 0x0FEFFFFF ? 0x0FEFFFFF : t;
-  return __int_as_float(t << 3);
-}
-__device__ __forceinline__ float norm_piece(float x, int bias, float scale, int& nonfinite) {
-  (void)bias;
-  nonfinite |= !isfinite(x);
-  return fabsf(x) * scale;
-}
-
-// Block-level broadcast of the loop decision made by thread 0.
-struct LoopCtl {
-  int go;       // 1: run another term
-  int k;        // index of the term to run
-  int status;
-  int bias;     // norm_piece bias of the current scale 2^-e0
-  float fscale; // 2^-e0 as a float (FP32 tiles)
-};
-
-__device__ __forceinline__ void set_norm_scale(LoopCtl& lc, int e0) {
-  lc.bias = norm_bias(e0);
-  const int ef = e0 < -126 ? -126 : (e0 > 126 ? 126 : e0);
-  lc.fscale = exp2f((float)-ef);
-}
-
-// Per-term column coefficients of the series, already divided by k (see series_kernel).
-template <typename T>
-struct SeriesTerm {
-  T kd[PHIC_MAX_R], ka[PHIC_MAX_R], kt[PHIC_MAX_R];
-};
-
-struct SeriesScalars {
-  double xi, tc[PHIC_MAX_R], cA[PHIC_MAX_R], cD[PHIC_MAX_R], cV[PHIC_MAX_R];
-  int s_int, bad, eA, nodiag;
-};
-
-template <typename T>
-struct RecoverScalars {
-  double xi, tB[PHIC_MAX_R], mu[PHIC_MAX_R], c[PHIC_MAX_R];
-  T coef[PHIC_MAX_R];
-  float fcoef[PHIC_MAX_R];
-  T cj[PHIC_MAX_P + 1][PHIC_MAX_R];
-  int s_int, series_terms, status, eA, nodiag;
-};
-
-}  // namespace
-
-// ===================================================================================================
-// Block series (Algorithm 3: setup and the first while loop)
-// ===================================================================================================
-// The recurrence is carried divided by k!: with X = A_1 (I kron T/s) = 2^eA B (I kron T/s),
-//   V~_k = V~_{k-1} Jsh / k,   D~_k = X D~_{k-1} / k + V~_k,   S = sum_k D~_k,   c2 = ||D~_k||_inf,
-// which equals the paper's D_k / k! and V_k / k! term by term but never holds the growing X^k D_1,
-// which would overflow FP32 (and, for a large ||X||, FP64) long before the terms become small.
 template <typename T, int CW, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) series_kernel(const SolveArgs a) {
-  __shared__ SeriesScalars sc;
-  __shared__ LoopCtl lc;
-  __shared__ SeriesTerm<T> tk;
-  __shared__ WarpParts wp;
-  Ctl* ctl = a.ctlS;
-  const int n = a.n, r = a.r, p = a.p;
-  const TileLayout L = a.S_lay;
-
-  if (threadIdx.x == 0) {
-    // s <- ceil(s max|t_i|);  mu = exp((xi/s) T);  V <- V (I kron 1^T mu/s);
-    // Jsh = (J kron Delta - xi I kron T)/s  (divided by s as in Algorithm 2)
-    const double xi = a.params->xi, s = a.params->s;
-    int bad = !isfinite(xi) || !(s >= 0.0) || !isfinite(s);
-    double tmax = 0.0;
-    for (int i = 0; i < r; ++i) tmax = fmax(tmax, fabs(a.t[i]));
-    double sint = ceil(s * tmax);
-    if (!(sint >= 1.0)) sint = 1.0;
-    if (sint > 2147483647.0) bad = 1;
-    const int si = bad ? 1 : (int)sint;
-    for (int i = 0; i < r; ++i) {
-      sc.tc[i] = a.t[i] / si;
-      sc.cA[i] = a.alpha[i] / si;
-      sc.cD[i] = -(xi * a.t[i]) / si;
-      sc.cV[i] = exp(xi * a.t[i] / si) / si;
-    }
-    sc.xi = xi;
-    sc.s_int = si;
-    sc.bad = bad;
-  }
-  __syncthreads();
-  if (sc.bad) {
-    if (threadIdx.x == 0) set_status(ctl, PHIC_INVALID_ARG);
-    return;
-  }
-  if (a.fault && blockIdx.x == 0 && gridDim.x > 1) return;  // test hook: never arrive at the barrier
-
-  const T* __restrict__ vals = static_cast<const T*>(a.vals);
-  CsrEnt<T>* __restrict__ ent = static_cast<CsrEnt<T>*>(a.A1);
-  const T* __restrict__ Vin = static_cast<const T*>(a.Vin);
-  T* __restrict__ S = static_cast<T*>(a.S);
-  const BlockRows br(n, L.Lp2);
-  const int lmask = L.Lp2 - 1;
-  const int c0 = (threadIdx.x & lmask) * CW;
-
-  T kV[CW];
-  int kI[CW];
-  bool kLive[CW], kUp[CW];
-  const T* kSrc[CW];
-#pragma unroll
-  for (int j = 0; j < CW; ++j) {
-    const int c = c0 + j;
-    kLive[j] = c < L.w;
-    const int b = kLive[j] ? c / r : 0, i = kLive[j] ? c - b * r : 0;
-    kI[j] = i;
-    kV[j] = (T)sc.cV[i];
-    kUp[j] = kLive[j] && b >= 2;
-    // column block b of V holds v0 (b = 0) or v_{p+1-b} (b >= 1): [v0, vp, ..., v1]
-    kSrc[j] = !kLive[j] ? nullptr
-              : (b == 0) ? (a.no_v0 ? nullptr : Vin)
-                         : Vin + (size_t)(p + 1 - b - a.no_v0) * n;
-  }
-  int bad = 0;
-  unsigned long long epoch = 0;  // grid barriers passed (thread 0)
-
-  // ---- setup pass 1: CSR checks, ||A - xi I||_inf, rows without a stored diagonal -------------------
-  {
-    unsigned long long mx = 0;
-    int nodiag = 0;
-    for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
-      const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
-      if (row < br.r1 && lane == 0) {
-        const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
-        if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) {
-          bad = 1;
-        } else {
-          bool shifted = false;
-          double rs = 0.0;
-          for (int q = b0; q < b1; ++q) {
-            const int col = __ldg(a.colidx + q);
-            if ((unsigned)col >= (unsigned)n) { bad = 1; continue; }
-            double v = (double)__ldg(vals + q);
-            if (!shifted && col == row) {
-              v -= sc.xi;
-              shifted = true;
-            }
-            rs += fabs(v);
-          }
-          if (!shifted) rs += fabs(sc.xi);
-          a.rowflag[row] = shifted ? 0 : 1;
-          nodiag |= !shifted;
-          umax(mx, rs);
-        }
-      }
-    }
-    warp_parts(wp, mx, (unsigned long long)nodiag, bad);
-  }
-  if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, 0, wp); },
-                      [&] {
-                        const double na = slot_get(ctl, 0, 0);
-                        sc.eA = (na > 0.0 && isfinite(na)) ? ilogb(na) + 1 : 0;  // ||B||_inf < 1
-                        sc.nodiag = slot_get(ctl, 0, 1) != 0.0;
-                        lc.status = read_status(ctl);
-                      }))
-    return;
-  if (lc.status != PHIC_OK) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      a.state->s_int = sc.s_int;
-      a.state->series_terms = 1;
-    }
-    return;
-  }
-
-  // ---- setup pass 2: entries of B = (A - xi I) 2^-eA, and k = 1: S = D = V -------------------------
-  {
-    const double scaleB = ldexp(1.0, -sc.eA);
-    T* V1 = static_cast<T*>(a.Vt[1]);
-    T* D1 = static_cast<T*>(a.Dt[1]);
-    unsigned long long mx = 0;
-    for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
-      const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
-      const bool act = row < br.r1 && lane < L.L;
-      T part = T(0);
-      if (act) {
-        if (lane == 0) {
-          const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
-          bool shifted = false;
-          for (int q = b0; q < b1; ++q) {  // subtract xi once from the stored diagonal, in FP64
-            const int col = __ldg(a.colidx + q);
-            double v = (double)__ldg(vals + q);
-            if (!shifted && col == row) {
-              v -= sc.xi;
-              shifted = true;
-            }
-            CsrEnt<T> e;
-            e.col = col;
-            e.v = (T)(v * scaleB);
-            ent[q] = e;
-          }
-        }
-        T x[CW];
-#pragma unroll
-        for (int j = 0; j < CW; ++j) {
-          x[j] = kSrc[j] ? kSrc[j][row] * kV[j] : T(0);
-          part += fabs(x[j]);
-        }
-        const size_t o = (size_t)row * L.ws + c0;
-        VecIO<T, CW>::st(V1 + o, x);
-        VecIO<T, CW>::st(D1 + o, x);
-        VecIO<T, CW>::st(S + o, x);
-      }
-      const T rs = group_sum(part, L.Lp2);
-      if (act && lane == 0) umax(mx, (double)rs);
-    }
-    warp_parts(wp, mx, 0ull, 0);
-  }
-
-  // Loop state, meaningful in thread 0 only.
-  int phase = 1, k = 1, status = PHIC_OK, e0 = 0;
-  double c1 = INFINITY, c2 = 0.0, nS = 0.0;
-  auto decide = [&]() {  // thread 0: evaluate  while c1 + c2 > tol ||S||  and prepare term k+1
-    int go = 0;
-    if (status == PHIC_OK && (!isfinite(c2) || !isfinite(nS))) status = PHIC_NONFINITE;  // NaN ends the test silently
-    if (status == PHIC_OK && c1 + c2 > a.tol * nS) {
-      if (k >= a.max_terms) status = PHIC_TERM_CAP;
-      else {
-        k += 1;
-        c1 = c2;
-        go = 1;
-        const double sB = ldexp(1.0, sc.eA);
-        for (int i = 0; i < r; ++i) {
-          tk.kd[i] = (T)(sc.cD[i] / k);
-          tk.ka[i] = (T)(sc.cA[i] / k);
-          tk.kt[i] = (T)(sc.tc[i] * sB / k);
-        }
-      }
-    }
-    lc.go = go;
-    lc.k = k;
-    lc.status = status;
-  };
-  slot_reset(ctl, phase);
-  if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, 1, wp); },
-                      [&] {
-                        status = read_status(ctl);
-                        c2 = slot_get(ctl, 1, 0);
-                        nS = c2;
-                        e0 = scale_exponent(c2);  // norms of later terms are carried in FP32 scaled by 2^-e0
-                        set_norm_scale(lc, e0);
-                        decide();
-                      }))
-    return;
-
-  // ---- k >= 2:  V <- V Jsh;  D <- A_1 D (I kron T/s) + V;  S <- S + D/k!  (divided by k!) ----------
-  const T xiB = (T)(-sc.xi * ldexp(1.0, -sc.eA));  // explicit shift for rows without a stored diagonal
-  const bool nodiag = sc.nodiag != 0;
-  while (lc.go) {
-    const int kk = lc.k;
-    ++phase;
-    slot_reset(ctl, phase);
-    T kD[CW], kA[CW], kT[CW];
-#pragma unroll
-    for (int j = 0; j < CW; ++j) {
-      kD[j] = tk.kd[kI[j]];
-      kA[j] = tk.ka[kI[j]];
-      kT[j] = tk.kt[kI[j]];
-    }
-    const T* __restrict__ Vo = static_cast<const T*>(a.Vt[(kk - 1) & 1]);
-    T* __restrict__ Vn = static_cast<T*>(a.Vt[kk & 1]);
-    const T* __restrict__ Do = static_cast<const T*>(a.Dt[(kk - 1) & 1]);
-    T* __restrict__ Dn = static_cast<T*>(a.Dt[kk & 1]);
-    unsigned long long mD = 0, mS = 0;
-    const int bias = lc.bias;
-    const float fscale = lc.fscale;
-    int nf = 0;
-    for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
-      const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
-      const bool act = row < br.r1 && lane < L.L;
-      float pD = 0.f, pS = 0.f;
-      if (act) {
-        const size_t o = (size_t)row * L.ws + c0;
-        T acc[CW];
-#pragma unroll
-        for (int j = 0; j < CW; ++j) acc[j] = T(0);
-        spmm_ent<T, CW>(a.rowptr, ent, Do, L.ws, c0, row, acc);
-        if (nodiag && a.rowflag[row]) {  // no stored diagonal: apply the shift explicitly
-          T own[CW];
-          VecIO<T, CW>::ld(Do + o, own);
-#pragma unroll
-          for (int j = 0; j < CW; ++j) acc[j] = fma(xiB, own[j], acc[j]);
-        }
-        T vo[CW], sv[CW], vn[CW], dn[CW];
-        VecIO<T, CW>::ld(Vo + o, vo);
-        VecIO<T, CW>::ld(S + o, sv);
-#pragma unroll
-        for (int j = 0; j < CW; ++j) {
-          // block b of the new V: -xi t_i/s times block b, plus alpha_i/s times block b-1 when b >= 2
-          T v = kD[j] * vo[j];
-          if (kUp[j]) v = fma(kA[j], Vo[o + j - r], v);
-          const T d = fma(acc[j], kT[j], v);
-          const T sn = sv[j] + d;
-          vn[j] = kLive[j] ? v : T(0);
-          dn[j] = kLive[j] ? d : T(0);
-          sv[j] = kLive[j] ? sn : T(0);
-          pD += norm_piece(dn[j], bias, fscale, nf);
-          pS += norm_piece(sv[j], bias, fscale, nf);
-        }
-        VecIO<T, CW>::st(Vn + o, vn);
-        VecIO<T, CW>::st(Dn + o, dn);
-        VecIO<T, CW>::st(S + o, sv);
-      }
-      const float rD = group_sum(pD, L.Lp2), rS = group_sum(pS, L.Lp2);
-      if (act && lane == 0) {
-        fmax_bits(mD, rD);
-        fmax_bits(mS, rS);
-      }
-    }
-    warp_parts(wp, mD, mS, 0, nf);
-    if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, phase, wp); },
-                        [&] {
-                          status = read_status(ctl);
-                          if (status == PHIC_OK && slot_nonfinite(ctl, phase)) status = PHIC_NONFINITE;
-                          c2 = slot_norm(ctl, phase, 0, e0);  // ||D_k||_inf / k!
-                          nS = slot_norm(ctl, phase, 1, e0);
-                          decide();
-                        }))
-      return;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (lc.status != PHIC_OK) set_status(ctl, lc.status);
-    a.state->s_int = sc.s_int;
-    a.state->series_terms = lc.k;
-    a.state->xi = sc.xi;
-    a.state->s = a.params->s;
-    a.state->eA = sc.eA;
-    a.state->nodiag = sc.nodiag;
-  }
+  __shared__ SeriesSmem<T> sm;
+  Team tm = grid_team(a.ctlS, a.spin_ns);
+  int phase = 0;
+  series_body<T, CW>(a, tm, sm, phase);
 }
 
-// ===================================================================================================
-// Recovery (Algorithm 3: first-block recovery, the for loop over j, the output)
-// ===================================================================================================
-namespace {
-// Block p of S Jt^j, column i, is sum_{a=1..p} S(:, (a, i)) (j alpha_i/s)^(p-a) / (p-a)!, because
-// Jt^j = exp(j J kron Delta / s) and (J^q)[a, p] = 1 exactly when a = p - q >= 1.
-template <typename T>
-__device__ void jt_power_coeffs(RecoverScalars<T>& rs, const SolveArgs& a, int j) {
-  const int p = a.p, r = a.r;
-  for (int idx = threadIdx.x; idx < p * r; idx += blockDim.x) {
-    const int aa = 1 + idx / r, i = idx % r;
-    const double x = (double)j * a.alpha[i] / rs.s_int;
-    double c = 1.0;
-    for (int q = 1; q <= p - aa; ++q) c = c * x / q;
-    rs.cj[aa][i] = (T)c;
-  }
-}
-}  // namespace
-
-// Recovery step j: F_k = A_1 F_{k-1} T / (s k) is carried as F_k = c_k G_k with G_k = B G_{k-1},
-// G_0 = F and c_k = c_{k-1} t_i 2^eA / (s k) per column, so that E <- E + F_k is fma(c_k, G_k, E).
 template <typename T, int CW, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) recover_kernel(const SolveArgs a) {
-  __shared__ RecoverScalars<T> sc;
-  __shared__ LoopCtl lc;
-  __shared__ WarpParts wp;
-  Ctl* ctl = a.ctlR;
-  const int n = a.n, r = a.r, p = a.p;
-  const TileLayout L = a.F_lay;
-  const int ws_s = a.S_lay.ws;
-
-  if (threadIdx.x == 0) {
-    sc.status = read_status(a.ctlS);
-    sc.s_int = a.state->s_int;
-    sc.series_terms = a.state->series_terms;
-    sc.xi = a.state->xi;
-    sc.eA = a.state->eA;
-    sc.nodiag = a.state->nodiag;
-    if (sc.status == PHIC_OK) {
-      const double sB = ldexp(1.0, sc.eA);
-      for (int i = 0; i < r; ++i) {
-        sc.tB[i] = a.t[i] * sB / sc.s_int;            // T <- I_2 kron T/s, times 2^eA for B
-        sc.mu[i] = exp(sc.xi * a.t[i] / sc.s_int);     // mu <- I_2 kron mu
-      }
-    }
-  }
-  __syncthreads();
-  long long rec_terms = 0;  // thread 0 of block 0 keeps the counts
-  int max_inner = 0;
-  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-  auto finish = [&](int st) {
-    if (leader) {
-      if (st != PHIC_OK) set_status(ctl, st);
-      const int s1 = read_status(a.ctlS);
-      const int fin = s1 != PHIC_OK ? s1 : read_status(ctl);
-      if (a.stats) {
-        a.stats->status = fin;
-        a.stats->s_int = sc.s_int;
-        a.stats->series_terms = sc.series_terms;
-        a.stats->max_inner_terms = max_inner;
-        a.stats->recovery_terms = rec_terms;
-        a.stats->spmm_count = (long long)(sc.series_terms - 1) + 1 + rec_terms;
-        a.stats->xi = sc.xi;
-        a.stats->s = a.state->s;
-      }
-    }
-  };
-  if (sc.status != PHIC_OK) {
-    finish(sc.status);
-    return;
-  }
-
-  const T* __restrict__ vals = static_cast<const T*>(a.vals);
-  const CsrEnt<T>* __restrict__ ent = static_cast<const CsrEnt<T>*>(a.A1);
-  const T* __restrict__ S = static_cast<const T*>(a.S);
-  const T* __restrict__ Vin = static_cast<const T*>(a.Vin);
-  T* __restrict__ E = static_cast<T*>(a.E);
-  const BlockRows br(n, L.Lp2);
-  const int lmask = L.Lp2 - 1;
-  const int c0 = (threadIdx.x & lmask) * CW;
-  int kI[CW];
-  bool kLive[CW], kBlkP[CW];
-  T kMu[CW], kTt[CW];
-#pragma unroll
-  for (int j = 0; j < CW; ++j) {
-    const int c = c0 + j;
-    kLive[j] = c < L.w;
-    kBlkP[j] = kLive[j] && c >= r;
-    kI[j] = !kLive[j] ? 0 : (c < r ? c : c - r);
-    kMu[j] = kLive[j] ? (T)sc.mu[kI[j]] : T(0);
-    kTt[j] = (T)a.t[kI[j]];
-  }
-  int bad = 0;
+  __shared__ RecoverSmem<T> sm;
+  Team tm = grid_team(a.ctlR, a.spin_ns);
   int phase = 0;
-  unsigned long long epoch = 0;  // grid barriers passed (thread 0)
-
-  // ---- F = S(:, [blk 0, blk p]);  F(:,1:r) <- A F(:,1:r) T + v0 1^T (unshifted A, t undivided) -----
-  {
-    T* F = static_cast<T*>(a.Ft[0]);
-    const T* v0 = a.no_v0 ? nullptr : Vin;
-    unsigned long long mx = 0;
-    for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
-      const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
-      const bool act = row < br.r1 && lane < L.L;
-      T part = T(0);
-      if (act) {
-        T f[CW];
-#pragma unroll
-        for (int j = 0; j < CW; ++j) {
-          T v = T(0);
-          if (kLive[j] && !kBlkP[j]) {
-            const int i = kI[j];
-            T acc = T(0);
-            const int beg = __ldg(a.rowptr + row), end = __ldg(a.rowptr + row + 1);
-            for (int q = beg; q < end; ++q) {
-              const int col = __ldg(a.colidx + q);
-              if ((unsigned)col >= (unsigned)n) { bad = 1; continue; }
-              acc = fma(__ldg(vals + q), S[(size_t)col * ws_s + i], acc);
-            }
-            v = fma(acc, kTt[j], v0 ? v0[row] : T(0));
-          } else if (kBlkP[j]) {
-            v = S[(size_t)row * ws_s + p * r + kI[j]];
-          }
-          f[j] = v;
-          part += fabs(v);
-        }
-        VecIO<T, CW>::st(F + (size_t)row * L.ws + c0, f);
-      }
-      const T rs = group_sum(part, L.Lp2);
-      if (act && lane == 0) umax(mx, (double)rs);
-    }
-    warp_parts(wp, mx, 0ull, bad);
-  }
-  // thread-0 loop state
-  int status = PHIC_OK, k = 0, e0 = 0;
-  double cF = 0.0, c1 = 0.0, c2 = 0.0, nE = 0.0;
-  if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, 0, wp); },
-                      [&] {
-                        status = read_status(ctl);
-                        cF = slot_get(ctl, 0, 0);
-                        lc.status = status;
-                      })) {
-    finish(PHIC_TIMEOUT);
-    return;
-  }
-  int cur = 0;
-  const T xiB = (T)(-sc.xi * ldexp(1.0, -sc.eA));
-  const bool nodiag = sc.nodiag != 0;
-
-  // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||: next term
-  auto decide = [&]() {
-    int go = 0;
-    if (status == PHIC_OK && (!isfinite(c2) || !isfinite(nE))) status = PHIC_NONFINITE;
-    if (status == PHIC_OK && c1 + c2 > a.tol * nE) {
-      if (k >= a.max_terms) status = PHIC_TERM_CAP;
-      else {
-        k += 1;
-        c1 = c2;
-        go = 1;
-        for (int i = 0; i < r; ++i) {
-          sc.c[i] = k == 1 ? sc.tB[i] : sc.c[i] * sc.tB[i] / k;  // c_k = (t_i 2^eA / s)^k / k!
-          sc.coef[i] = (T)sc.c[i];
-          sc.fcoef[i] = (float)sc.c[i];
-        }
-      }
-    }
-    lc.go = go;
-    lc.k = k;
-    lc.status = status;
-  };
-
-  // ---- for j = 1 : s-1 ------------------------------------------------------------------------------
-  for (int jstep = 1; jstep <= sc.s_int - 1 && lc.status == PHIC_OK; ++jstep) {
-    if (threadIdx.x == 0) {
-      k = 0;
-      c1 = INFINITY;
-      c2 = cF;
-      nE = cF;
-      e0 = scale_exponent(cF);  // norms of this step's terms are carried in FP32 scaled by 2^-e0
-      set_norm_scale(lc, e0);
-      decide();
-    }
-    __syncthreads();
-    while (lc.go) {
-      const int kk = lc.k;
-      ++phase;
-      slot_reset(ctl, phase);
-      T kC[CW];
-      float kF[CW];
-#pragma unroll
-      for (int j = 0; j < CW; ++j) {
-        kC[j] = kLive[j] ? sc.coef[kI[j]] : T(0);
-        kF[j] = kLive[j] ? sc.fcoef[kI[j]] : 0.f;
-      }
-      const T* __restrict__ Go = static_cast<const T*>(a.Ft[cur]);
-      T* __restrict__ Gn = static_cast<T*>(a.Ft[cur ^ 1]);
-      unsigned long long mF = 0, mE = 0;
-      const int bias = lc.bias;
-      const float fscale = lc.fscale;
-      int nf = 0;
-      constexpr int NR = sizeof(T) == 4 ? PHIC_ROWS_F32 : 1;  // rows in flight per thread
-      const int lane = threadIdx.x & lmask;
-      for (long long it0 = threadIdx.x; it0 < br.padded; it0 += (long long)NR * kBlock) {
-        int row[NR];
-        bool act[NR];
-#pragma unroll
-        for (int u = 0; u < NR; ++u) {
-          const long long it = it0 + (long long)u * kBlock;
-          row[u] = br.r0 + (int)(it >> br.shift);
-          act[u] = it < br.padded && row[u] < br.r1 && lane < L.L;
-        }
-        T acc[NR][CW];
-        spmm_rows<T, CW, NR>(a.rowptr, ent, Go, L.ws, c0, row, act, acc);
-        float pF[NR], pE[NR];
-#pragma unroll
-        for (int u = 0; u < NR; ++u) {
-          pF[u] = 0.f;
-          pE[u] = 0.f;
-          if (act[u]) {
-            const size_t o = (size_t)row[u] * L.ws + c0;
-            const bool shift_row = nodiag && a.rowflag[row[u]];
-            T e[CW];
-            if (kk == 1 || shift_row) {
-              T own[CW];
-              VecIO<T, CW>::ld(Go + o, own);
-              if (shift_row) {
-#pragma unroll
-                for (int j = 0; j < CW; ++j) acc[u][j] = fma(xiB, own[j], acc[u][j]);
-              }
-              if (kk == 1) {
-#pragma unroll
-                for (int j = 0; j < CW; ++j) e[j] = own[j];  // E = F at the start of the step
-              }
-            }
-            if (kk != 1) VecIO<T, CW>::ld(E + o, e);
-#pragma unroll
-            for (int j = 0; j < CW; ++j) {
-              // F_k = c_k G_k;  E <- E + F_k
-              e[j] = fma(kC[j], acc[u][j], e[j]);
-              pF[u] += kF[j] * norm_piece(acc[u][j], bias, fscale, nf);
-              pE[u] += norm_piece(e[j], bias, fscale, nf);
-            }
-            VecIO<T, CW>::st(Gn + o, acc[u]);
-            VecIO<T, CW>::st(E + o, e);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < NR; ++u) {
-          const float rF = group_sum(pF[u], L.Lp2), rE = group_sum(pE[u], L.Lp2);
-          if (act[u] && lane == 0) {
-            fmax_bits(mF, rF);
-            fmax_bits(mE, rE);
-          }
-        }
-      }
-      warp_parts(wp, mF, mE, 0, nf);
-      cur ^= 1;
-      if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, phase, wp); },
-                          [&] {
-                            status = read_status(ctl);
-                            if (status == PHIC_OK && slot_nonfinite(ctl, phase)) status = PHIC_NONFINITE;
-                            c2 = slot_norm(ctl, phase, 0, e0);
-                            nE = slot_norm(ctl, phase, 1, e0);
-                            decide();
-                          })) {
-        finish(PHIC_TIMEOUT);
-        return;
-      }
-    }
-    if (leader) {
-      rec_terms += lc.k;
-      max_inner = lc.k > max_inner ? lc.k : max_inner;
-    }
-    if (lc.status != PHIC_OK) break;
-
-    // ---- E <- E mu;  S <- S Jt;  F <- E + S(:, [blk 0, blk p]);  F(:,1:r) <- E(:,1:r) -------------
-    ++phase;
-    slot_reset(ctl, phase);
-    jt_power_coeffs(sc, a, jstep);
-    __syncthreads();
-    {
-      T* __restrict__ F = static_cast<T*>(a.Ft[cur]);
-      unsigned long long mx = 0;
-      for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
-        const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
-        const bool act = row < br.r1 && lane < L.L;
-        T part = T(0);
-        if (act) {
-          const size_t o = (size_t)row * L.ws + c0;
-          T e[CW];
-          VecIO<T, CW>::ld(E + o, e);
-#pragma unroll
-          for (int j = 0; j < CW; ++j) {
-            T v = e[j] * kMu[j];
-            if (kBlkP[j]) {
-              const int i = kI[j];
-              const T* srow = S + (size_t)row * ws_s;
-              for (int aa = 1; aa <= p; ++aa) v = fma(srow[aa * r + i], sc.cj[aa][i], v);
-            }
-            e[j] = kLive[j] ? v : T(0);
-            part += fabs(e[j]);
-          }
-          VecIO<T, CW>::st(F + o, e);
-        }
-        const T rs = group_sum(part, L.Lp2);
-        if (act && lane == 0) umax(mx, (double)rs);
-      }
-      warp_parts(wp, mx, 0ull, 0);
-      if (!grid_sync_lead(ctl, epoch, a.spin_ns, [&] { parts_to_slots(ctl, phase, wp); },
-                          [&] {
-                            cF = slot_get(ctl, phase, 0);
-                            status = read_status(ctl);
-                            lc.status = status;
-                          })) {
-        finish(PHIC_TIMEOUT);
-        return;
-      }
-    }
-  }
-
-  // ---- w_i = F(:, i) + alpha_i F(:, r+i)   (p = 0: w_i = F(:, i) = exp(t_i A) v0) -------------------
-  if (lc.status == PHIC_OK) {
-    const T* __restrict__ F = static_cast<const T*>(a.Ft[cur]);
-    T* __restrict__ W = static_cast<T*>(a.W);
-    const long long total = (long long)n * r;
-    const long long stride = (long long)gridDim.x * kBlock;
-    for (long long idx = (long long)blockIdx.x * kBlock + threadIdx.x; idx < total; idx += stride) {
-      const int i = (int)(idx / n), row = (int)(idx - (long long)i * n);
-      const T* frow = F + (size_t)row * L.ws;
-      W[idx] = (p == 0) ? frow[i] : fma((T)a.alpha[i], frow[r + i], frow[i]);
-    }
-  }
-  finish(lc.status);
+  recover_body<T, CW>(a, tm, sm, phase, 0x7fffffff);
 }
 
 // ---------------------------------------------------------------------------------------------------
