@@ -17,9 +17,10 @@
  * Conventions
  *   - Every pointer documented "device" must point to memory of the current CUDA device; "host"
  *     pointers are read before the call returns.  Nothing is retained after a call returns.
- *   - Ownership: the caller owns every buffer, including the workspace.  The library allocates no
- *     memory, keeps no state between calls other than cached launch configurations, and never
- *     synchronises the stream.  All work is enqueued on `stream` (0 = legacy default stream).
+ *   - Ownership: the caller owns every device buffer, including the workspace.  The library allocates
+ *     no device memory, keeps no state between calls other than cached launch configurations and the
+ *     host-side batch handles it returns, and never synchronises the stream (except the batch set-up
+ *     and autotuning calls, which say so).  All work is enqueued on `stream` (0 = legacy default stream).
  *   - Device-side outcomes (non-finite norms, the term cap, a timed-out grid barrier, a bad column
  *     index) are written as a phic_status into phic_params.status / phic_stats.status in device
  *     memory; the return value of a call only reports what the host could check before enqueuing
@@ -180,6 +181,232 @@ phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, c
 phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t r, const void* V, const double* t,
                                const double* alpha, double tol, const phic_params* params_dev, uint32_t flags,
                                int32_t max_terms, void* W, phic_stats* stats_dev, int32_t prec, phic_stream_t stream);
+
+/* ---- Batched solves -------------------------------------------------------------------------------
+ * Many independent instances (each its own A, p, r, t, alpha, tol and precision) in ONE persistent
+ * cooperative launch.  The paper solves one instance per call; this interface serves workloads of many
+ * uneven problems (an integrator over many operators, a request stream).  Each instance is run by a
+ * team of CTAs with the same kernels' code as phic_select_params / phic_solve, synchronised by a
+ * bounded barrier of its own; a host planner sizes the teams from n (phic_batch_config.rows_per_cta)
+ * and orders the work longest first over the launch's CTAs.  A solve's result does not depend on its
+ * team size or on the other instances in the launch (the truncation tests use infinity norms, which are
+ * maxima); Algorithm 1's sums of squares are rounded per team, so with PHIC_BATCH_SELECT the selected
+ * s and xi can differ in the last bits from phic_select_params.
+ * The handle (phic_batch) lives in host memory allocated by the library; every device buffer,
+ * including the workspace, is the caller's. */
+
+#define PHIC_BATCH_SELECT 0x100u   /* run Algorithm 1 for the instance first, writing *params (its tol is the
+                                      item's tol; m, delta, seed and max_evals come from the options) */
+#define PHIC_BATCH_NO_SOLVE 0x200u /* run Algorithm 1 only (requires PHIC_BATCH_SELECT) */
+
+/* One instance of a batch. */
+typedef struct {
+  phic_csr A;              /* operator (device arrays, checked on the device as in phic_solve) */
+  int32_t p, r;            /* as in phic_solve */
+  uint32_t flags;          /* PHIC_NO_V0, PHIC_BATCH_SELECT, PHIC_BATCH_NO_SOLVE */
+  int32_t max_terms;       /* as in phic_solve (<= 0 selects 610) */
+  const void* V;           /* device, as in phic_solve */
+  void* W;                 /* device, as in phic_solve (may be NULL with PHIC_BATCH_NO_SOLVE) */
+  phic_params* params;     /* device: read by the solve; written first when PHIC_BATCH_SELECT is set */
+  phic_stats* stats;       /* device or NULL, as in phic_solve */
+  const double* v_select;  /* device unit vector for Algorithm 1, or NULL (splitmix64 of the options' seed) */
+  double tol;              /* truncation tolerance, as in phic_solve */
+  double s_hint;           /* host estimate of s for the planner's cost model only (<= 0: one scaling step) */
+  double t[PHIC_MAX_R];    /* abscissae t_1..t_r (host copy) */
+  double alpha[PHIC_MAX_R];/* weights alpha_1..alpha_r (host copy) */
+} phic_batch_item;
+
+/* Launch shape of a batch (the autotuner's search space). */
+typedef struct {
+  int32_t rows_per_cta;   /* an instance of n rows gets ceil(n / rows_per_cta) CTAs, at most the grid
+                             (<= 0 selects 4096; at least 256) */
+  int32_t blocks_per_sm;  /* resident CTAs per SM: 2 or 3 (<= 0 selects 2) */
+  int32_t max_steps;      /* recovery outer steps per instance per launch (<= 0: run to the end).  With a
+                             bound, a launch may stop an instance between outer steps; launching the
+                             same batch again (phic_batch_resume) continues it. */
+  int32_t reserved;
+} phic_batch_config;
+
+/* Planner output. */
+typedef struct {
+  int32_t grid;            /* CTAs of the launch (SMs x blocks_per_sm) */
+  int32_t blocks_per_sm;
+  int32_t count;           /* instances */
+  int32_t max_team;        /* largest team */
+  int64_t entries;         /* schedule entries (sum of team sizes) */
+  double est_makespan_us;  /* cost-model estimate of the launch */
+  double est_busy_frac;    /* estimated busy CTA time / (grid x makespan) */
+} phic_batch_info;
+
+typedef struct phic_batch phic_batch;
+
+/* Device workspace bytes of a batch: per instance the workspaces of phic_select_params (with
+ * PHIC_BATCH_SELECT) and phic_solve (unless PHIC_BATCH_NO_SOLVE), plus the control blocks, the
+ * instance table and the schedule.  opts may be NULL (defaults). */
+phic_status phic_batch_workspace_size(const phic_batch_item* items, int32_t count, const phic_select_opts* opts,
+                                      size_t* bytes);
+
+/* Checks the items (host side, as phic_solve does), lays out ws (device, 256-byte aligned), plans the
+ * teams and the schedule for cfg (NULL: defaults) and copies the instance table and the schedule into
+ * ws on `stream`, synchronising `stream` once before returning (set-up call, not for capture).  items
+ * is read before the call returns.  *out receives the handle. */
+phic_status phic_batch_create(const phic_batch_item* items, int32_t count, const phic_select_opts* opts,
+                              const phic_batch_config* cfg, void* ws, size_t ws_bytes, phic_stream_t stream,
+                              phic_batch** out);
+
+/* Enqueues the batch: a memset of the instances' control blocks and one cooperative launch.  No host
+ * synchronisation, no allocation: the pair can be captured into a CUDA graph and replayed; each launch
+ * recomputes every instance from V (and, with PHIC_BATCH_SELECT, from A). */
+phic_status phic_batch_launch(phic_batch* b, phic_stream_t stream);
+
+/* For a batch created with max_steps > 0: enqueues the next slice, in which every instance continues its
+ * recovery from where the previous launch stopped (instances already finished do no work).  Call it after
+ * one phic_batch_launch until phic_stats.status of every instance is final (the host reads
+ * phic_stats.recovery_terms / the state to know; see phic_batch_pending). */
+phic_status phic_batch_resume(phic_batch* b, phic_stream_t stream);
+
+/* Number of instances not finished after the work enqueued so far: enqueues a small kernel on `stream`
+ * that counts them into *pending_dev (device int32). */
+phic_status phic_batch_pending(const phic_batch* b, int32_t* pending_dev, phic_stream_t stream);
+
+phic_status phic_batch_info_get(const phic_batch* b, phic_batch_info* info);
+
+/* Releases the handle (host memory only). */
+void phic_batch_destroy(phic_batch* b);
+
+/* The planner alone, on the host (no CUDA call; the items' device pointers are not dereferenced): the
+ * team size of each instance (team[count]) and the schedule of a launch of `grid` CTAs as
+ * sched_ptr[grid + 1] and (instance, rank) pairs sched[2 * entries], as phic_batch_create would build
+ * them for cfg.  Returns PHIC_WORKSPACE_TOO_SMALL (with *entries set) when sched_cap pairs do not fit. */
+phic_status phic_batch_plan_host(const phic_batch_item* items, int32_t count, const phic_select_opts* opts,
+                                 const phic_batch_config* cfg, int32_t grid, int32_t* team, int32_t* sched_ptr,
+                                 int32_t* sched, int64_t sched_cap, int64_t* entries, double* makespan_us);
+
+/* Autotuner: plans and launches the batch with each candidate configuration (all on `stream`, with
+ * CUDA events around `reps` launches after one warm-up launch), keeps the fastest by median time and
+ * writes it to *best and its median milliseconds to *best_ms.  candidates NULL (or ncand <= 0) searches
+ * rows_per_cta in {512, 1024, 2048, 4096, 8192, 16384} x blocks_per_sm in {2, 3}.  The batch's outputs
+ * are written by every trial launch.  Synchronises `stream`. */
+phic_status phic_batch_autotune(const phic_batch_item* items, int32_t count, const phic_select_opts* opts, void* ws,
+                                size_t ws_bytes, const phic_batch_config* candidates, int32_t ncand, int32_t reps,
+                                phic_stream_t stream, phic_batch_config* best, double* best_ms);
+
+/* ---- Serving loop ----------------------------------------------------------------------------------
+ * A request loop with continuous batching (an extension; the paper has no counterpart).  A worker thread
+ * owned by the server admits submitted solves in arrival order while their device footprint (operator,
+ * vectors, result, Algorithm 1's basis and Algorithm 3's workspace) fits in the arena, copies their
+ * inputs to the device on a copy stream, and runs every loaded request together in slices: each slice
+ * is one batched launch in which new requests run Algorithm 1, the series and up to max_steps recovery
+ * steps, and requests already running continue their recovery by up to max_steps steps.  Requests that
+ * arrive while a slice runs are admitted and loaded meanwhile and join the next slice; finished results
+ * are copied back on the copy stream while the next slice runs, and their memory is released.
+ * Operators and Taylor state stay on the device for a request's whole life.  A request's result does
+ * not depend on the other requests or on how its work was sliced (see the batched launch above).
+ * Thread-safe: submit / query / wait may be called from any host thread. */
+
+typedef struct {
+  void* arena;               /* device memory managed by the server (caller-owned, 256-byte aligned) */
+  size_t arena_bytes;
+  int32_t rows_per_cta;      /* team sizing of the slices (<= 0 selects 4096) */
+  int32_t blocks_per_sm;     /* 2 or 3 (<= 0 selects 2) */
+  int32_t max_steps;         /* recovery outer steps per request per slice (<= 0 selects 8) */
+  int32_t max_active;        /* requests per slice (<= 0 selects 1024) */
+  int32_t device;            /* CUDA device of the worker thread */
+  int32_t m;                 /* Algorithm 1's degree (<= 0 selects 61); delta 0.8, seed 0x5EED, 200 evaluations */
+} phic_server_config;
+
+/* An operator registered with the server: uploaded once, Algorithm 1 run once, then shared by every
+ * request that names it (the paper reuses (s, xi) across calls with the same A, Section 6).  HOST arrays,
+ * read until the operator is ready. */
+typedef struct {
+  int64_t n, nnz;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const void* values;
+  int32_t prec;
+  int32_t pad;
+} phic_operator;
+
+/* One solve request; every array is in HOST memory and must stay valid (W unread) until the request is
+ * reported done.  Page-locked memory lets the copies overlap with the kernels.  With op != 0 the request
+ * uses that registered operator (n and prec must match; rowptr, colidx, values and nnz are ignored) and
+ * its Algorithm 1 result, with s = s0 f* / (tol m!)^(1/m) for the request's tol; otherwise it brings its
+ * own operator and Algorithm 1 runs in its first slice. */
+typedef struct {
+  int64_t n, nnz;
+  const int32_t* rowptr;     /* n + 1 */
+  const int32_t* colidx;     /* nnz */
+  const void* values;        /* nnz of prec */
+  const void* V;             /* (p+1) x n of prec, as in phic_solve (p x n with PHIC_NO_V0) */
+  void* W;                   /* r x n of prec: the result, written before the request is reported done */
+  int32_t prec, p, r;
+  uint32_t flags;            /* PHIC_NO_V0 */
+  double tol;                /* truncation tolerance (and Algorithm 1's) */
+  int32_t max_terms;         /* as in phic_solve (<= 0 selects 610) */
+  int32_t pad;
+  int64_t op;                /* registered operator, or 0 */
+  double t[PHIC_MAX_R];
+  double alpha[PHIC_MAX_R];
+} phic_request;
+
+typedef enum {
+  PHIC_REQ_QUEUED = 0,   /* waiting for device memory */
+  PHIC_REQ_LOADING = 1,  /* inputs being copied in */
+  PHIC_REQ_RUNNING = 2,  /* taking part in slices */
+  PHIC_REQ_COPYING = 3,  /* result being copied out */
+  PHIC_REQ_DONE = 4      /* W holds the result (or status reports the failure) */
+} phic_request_state;
+
+typedef struct {
+  int32_t state;            /* phic_request_state */
+  int32_t status;           /* phic_status of the request (valid when done) */
+  int64_t submit_ns;        /* steady-clock times: submission, admission (memory granted), done */
+  int64_t admit_ns;
+  int64_t done_ns;
+  int32_t slices;           /* slices the request took part in */
+  int32_t pad;
+  phic_params params;       /* Algorithm 1's output (valid when done) */
+  phic_stats stats;         /* Algorithm 3's record (valid when done) */
+} phic_request_info;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed;
+  int64_t slices;           /* batched launches */
+  int64_t max_slice_requests;
+  int64_t arena_in_use, arena_peak;
+  double gpu_busy_ms;       /* sum of the slices' device durations */
+} phic_server_counters;
+
+typedef struct phic_server phic_server;
+
+/* Starts the worker thread.  The arena must outlive the server. */
+phic_status phic_server_create(const phic_server_config* cfg, phic_server** out);
+
+/* Queues a request (host arguments checked as in phic_solve); *id identifies it.  PHIC_WORKSPACE_TOO_SMALL:
+ * the request can never fit in the arena. */
+phic_status phic_server_submit(phic_server* srv, const phic_request* req, int64_t* id);
+
+/* Registers an operator (copied in and run through Algorithm 1 as the server's memory allows); *op_id
+ * names it in requests.  Requests may name it at once: they wait until it is ready. */
+phic_status phic_server_add_operator(phic_server* srv, const phic_operator* op, int64_t* op_id);
+
+/* Algorithm 1's result for a registered operator (status PHIC_OK once ready; *ready 0 before). */
+phic_status phic_server_operator_params(phic_server* srv, int64_t op_id, int32_t* ready, phic_params* params);
+
+/* Releases a registered operator once no admitted or queued request uses it. */
+phic_status phic_server_remove_operator(phic_server* srv, int64_t op_id);
+
+/* Current state of a request. */
+phic_status phic_server_query(phic_server* srv, int64_t id, phic_request_info* info);
+
+/* Waits until the request is done (timeout_ms < 0: no limit); PHIC_TIMEOUT when the limit passed first. */
+phic_status phic_server_wait(phic_server* srv, int64_t id, double timeout_ms, phic_request_info* info);
+
+phic_status phic_server_counters_get(phic_server* srv, phic_server_counters* out);
+
+/* Stops the worker after the slice in flight, waits for the device, and releases the server (requests not
+ * done are dropped: their W is not written). */
+void phic_server_destroy(phic_server* srv);
 
 /* Bound on one grid-barrier wait of phic_solve in milliseconds (default 2000).  Applies to later calls. */
 void phic_set_spin_limit_ms(double ms);

@@ -221,3 +221,340 @@ def phimv(A, V, t, alpha, tol: float = 2.0**-53, params: torch.Tensor | None = N
         capi.check(read_params(P)["status"], "phic_select_params (device)")
         capi.check(read_stats(st)["status"], "phic_solve (device)")
     return W.cpu() if host_io else W
+
+
+# ---- batched launches ------------------------------------------------------------------------------
+@dataclass
+class BatchItem:
+    """One instance of a batch.  ``V`` is (p+1, n) (p rows with ``no_v0``) in the precision of A's
+    values; ``params``, ``W`` and ``stats`` are allocated when not given.  ``select`` runs Algorithm 1
+    for the instance at the start of its team's work; ``s_hint`` (host) only steers the planner."""
+
+    A: DeviceCSR
+    V: torch.Tensor | None
+    t: tuple
+    alpha: tuple
+    tol: float = 2.0**-53
+    select: bool = True
+    solve: bool = True
+    no_v0: bool = False
+    s_hint: float = 0.0
+    max_terms: int = 0
+    params: torch.Tensor | None = None
+    W: torch.Tensor | None = None
+    stats: torch.Tensor | None = None
+    v_select: torch.Tensor | None = None
+
+    def prepare(self):
+        dev = self.A.rowptr.device
+        dt = _TORCH_DT[self.A.prec]
+        t = np.atleast_1d(np.asarray(self.t, dtype=np.float64))
+        if self.params is None:
+            self.params = new_params(dev)
+        if self.solve:
+            if self.V is None or self.V.dtype != dt or not self.V.is_cuda or not self.V.is_contiguous() or \
+                    self.V.dim() != 2 or self.V.shape[1] != self.A.n:
+                raise ValueError(f"V must be a contiguous CUDA {dt} tensor of shape (p+1, n)")
+            if self.W is None:
+                self.W = torch.empty((t.size, self.A.n), dtype=dt, device=dev)
+            if self.stats is None:
+                self.stats = new_stats(dev)
+        return self
+
+    @property
+    def p(self) -> int:
+        if self.V is None:
+            return 0
+        return self.V.shape[0] if self.no_v0 else self.V.shape[0] - 1
+
+    def struct(self) -> capi.phic_batch_item:
+        t = np.atleast_1d(np.asarray(self.t, dtype=np.float64))
+        a = np.atleast_1d(np.asarray(self.alpha, dtype=np.float64))
+        if t.size != a.size or not 1 <= t.size <= capi.PHIC_MAX_R:
+            raise ValueError("t and alpha must have the same length, at most PHIC_MAX_R")
+        it = capi.phic_batch_item()
+        it.A = self.A.struct()
+        it.p, it.r = self.p, int(t.size)
+        it.flags = (capi.PHIC_NO_V0 if self.no_v0 else 0) | (capi.PHIC_BATCH_SELECT if self.select else 0) | \
+            (0 if self.solve else capi.PHIC_BATCH_NO_SOLVE)
+        it.max_terms = int(self.max_terms)
+        it.V = self.V.data_ptr() if self.V is not None else None
+        it.W = self.W.data_ptr() if self.W is not None else None
+        it.params = self.params.data_ptr()
+        it.stats = self.stats.data_ptr() if self.stats is not None else None
+        it.v_select = self.v_select.data_ptr() if self.v_select is not None else None
+        it.tol, it.s_hint = float(self.tol), float(self.s_hint)
+        for i in range(t.size):
+            it.t[i], it.alpha[i] = float(t[i]), float(a[i])
+        return it
+
+
+def _select_opts(m=61, delta=0.8, seed=0x5EED, max_evals=200):
+    opts = capi.phic_select_opts()
+    capi.load().phic_select_opts_default(ctypes.byref(opts))
+    opts.m, opts.delta, opts.seed, opts.max_evals = int(m), float(delta), int(seed) & (2**64 - 1), int(max_evals)
+    return opts
+
+
+def _item_array(items):
+    arr = (capi.phic_batch_item * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = it.prepare().struct()
+    return arr
+
+
+def _config(cfg):
+    if cfg is None:
+        return None
+    if isinstance(cfg, capi.phic_batch_config):
+        return cfg
+    return capi.phic_batch_config(int(cfg.get("rows_per_cta", 0)), int(cfg.get("blocks_per_sm", 0)),
+                                  int(cfg.get("max_steps", 0)), 0)
+
+
+def batch_workspace_bytes(items, select_opts=None) -> int:
+    arr = _item_array(items)
+    out = ctypes.c_size_t(0)
+    opts = select_opts or _select_opts()
+    capi.check(capi.load().phic_batch_workspace_size(arr, len(items), ctypes.byref(opts), ctypes.byref(out)),
+               "phic_batch_workspace_size")
+    return int(out.value)
+
+
+class Batch:
+    """Many independent instances in one persistent cooperative launch (``phic_batch_*``).
+
+        b = Batch([BatchItem(A1, V1, t1, a1), BatchItem(A2, V2, t2, a2, tol=2**-24), ...])
+        b.launch()                 # one kernel launch for every instance (capturable in a CUDA graph)
+        W1 = b.items[0].W
+
+    ``config`` is a dict with ``rows_per_cta``, ``blocks_per_sm`` and ``max_steps`` (see
+    phic_batch_config) or None for the defaults; ``autotune`` picks one by timing the batch."""
+
+    def __init__(self, items, config=None, select_opts=None, workspace: torch.Tensor | None = None, stream=None):
+        self.lib = capi.load()
+        self.items = list(items)
+        self.arr = _item_array(self.items)
+        self.opts = select_opts or _select_opts()
+        nbytes = batch_workspace_bytes(self.items, self.opts)
+        dev = self.items[0].A.rowptr.device
+        self.ws = workspace if workspace is not None and workspace.numel() >= nbytes else \
+            torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+        self.cfg = _config(config)
+        h = ctypes.c_void_p(0)
+        st = self.lib.phic_batch_create(self.arr, len(self.items), ctypes.byref(self.opts),
+                                        ctypes.byref(self.cfg) if self.cfg is not None else None,
+                                        self.ws.data_ptr(), self.ws.numel(), _stream_handle(stream), ctypes.byref(h))
+        capi.check(st, "phic_batch_create")
+        self.handle = h
+        self._pending = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def launch(self, stream=None):
+        capi.check(self.lib.phic_batch_launch(self.handle, _stream_handle(stream)), "phic_batch_launch")
+
+    def resume(self, stream=None):
+        capi.check(self.lib.phic_batch_resume(self.handle, _stream_handle(stream)), "phic_batch_resume")
+
+    def pending(self, stream=None) -> int:
+        capi.check(self.lib.phic_batch_pending(self.handle, self._pending.data_ptr(), _stream_handle(stream)),
+                   "phic_batch_pending")
+        return int(self._pending.item())
+
+    def info(self) -> dict:
+        inf = capi.phic_batch_info()
+        capi.check(self.lib.phic_batch_info_get(self.handle, ctypes.byref(inf)), "phic_batch_info_get")
+        return {k: getattr(inf, k) for k, _ in capi.phic_batch_info._fields_}
+
+    def stats(self) -> list:
+        return [read_stats(it.stats) if it.stats is not None else None for it in self.items]
+
+    def params(self) -> list:
+        return [read_params(it.params) for it in self.items]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.phic_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(items, candidates=None, reps: int = 3, select_opts=None, workspace: torch.Tensor | None = None,
+             stream=None):
+    """Times the batch under each candidate configuration (dicts as for Batch) and returns
+    (best config dict, its median ms).  None searches the library's default grid."""
+    lib = capi.load()
+    items = list(items)
+    arr = _item_array(items)
+    opts = select_opts or _select_opts()
+    nbytes = batch_workspace_bytes(items, opts)
+    dev = items[0].A.rowptr.device
+    ws = workspace if workspace is not None and workspace.numel() >= nbytes else \
+        torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+    cand = None
+    ncand = 0
+    if candidates:
+        cand = (capi.phic_batch_config * len(candidates))(*[_config(c) for c in candidates])
+        ncand = len(candidates)
+    best = capi.phic_batch_config()
+    ms = ctypes.c_double(0.0)
+    st = lib.phic_batch_autotune(arr, len(items), ctypes.byref(opts), ws.data_ptr(), ws.numel(), cand, ncand,
+                                 int(reps), _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms))
+    capi.check(st, "phic_batch_autotune")
+    return {"rows_per_cta": best.rows_per_cta, "blocks_per_sm": best.blocks_per_sm, "max_steps": best.max_steps}, \
+        float(ms.value)
+
+
+# ---- serving loop ----------------------------------------------------------------------------------
+def _info_dict(info: capi.phic_request_info) -> dict:
+    p, s = info.params, info.stats
+    return dict(state=info.state, status=info.status, submit_ns=info.submit_ns, admit_ns=info.admit_ns,
+                done_ns=info.done_ns, slices=info.slices,
+                params=dict(xi=p.xi, s=p.s, s0=p.s0, f_star=p.f_star, r=p.r, evals=p.evals, status=p.status),
+                stats=dict(status=s.status, s_int=s.s_int, series_terms=s.series_terms,
+                           max_inner_terms=s.max_inner_terms, recovery_terms=s.recovery_terms,
+                           spmm_count=s.spmm_count, xi=s.xi, s=s.s))
+
+
+def _host(a, dtype, pin):
+    x = torch.as_tensor(np.ascontiguousarray(a)).to(dtype)
+    return x.pin_memory() if pin else x.contiguous()
+
+
+class HostOperator:
+    """Host-side (page-locked) CSR arrays of an operator to register with a Server."""
+
+    def __init__(self, A, prec: str = "f64", pin: bool = True):
+        dt = torch.float32 if prec in ("f32", capi.PHIC_F32, torch.float32) else torch.float64
+        self.rowptr = _host(A.rowptr, torch.int32, pin)
+        self.colidx = _host(A.colidx, torch.int32, pin)
+        self.values = _host(A.values, dt, pin)
+        self.n, self.nnz, self.prec = int(A.n), int(self.colidx.numel()), prec_of(dt)
+
+    def struct(self) -> capi.phic_operator:
+        return capi.phic_operator(self.n, self.nnz, self.rowptr.data_ptr(), self.colidx.data_ptr(),
+                                  self.values.data_ptr(), self.prec, 0)
+
+
+class HostRequest:
+    """Host-side (page-locked) buffers of one request: the CSR operator (or a registered operator's id),
+    V and the result W."""
+
+    def __init__(self, A, V, t, alpha, tol: float = 2.0**-53, prec: str = "f64", no_v0: bool = False,
+                 max_terms: int = 0, pin: bool = True, op: int = 0):
+        dt = torch.float32 if prec in ("f32", capi.PHIC_F32, torch.float32) else torch.float64
+        self.op = int(op)
+        if self.op:
+            self.rowptr = self.colidx = self.values = None
+            n, nnz = int(A), 0
+        else:
+            self.rowptr = _host(A.rowptr, torch.int32, pin)
+            self.colidx = _host(A.colidx, torch.int32, pin)
+            self.values = _host(A.values, dt, pin)
+            n, nnz = int(A.n), int(self.colidx.numel())
+        self.V = _host(V, dt, pin)
+        self.t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+        self.alpha = np.atleast_1d(np.asarray(alpha, dtype=np.float64))
+        self.n, self.nnz = n, nnz
+        self.prec = prec_of(dt)
+        self.no_v0 = bool(no_v0)
+        self.p = self.V.shape[0] if no_v0 else self.V.shape[0] - 1
+        self.r = int(self.t.size)
+        self.W = torch.empty((self.r, self.n), dtype=dt, pin_memory=pin)
+        self.tol = float(tol)
+        self.max_terms = int(max_terms)
+
+    def struct(self) -> capi.phic_request:
+        q = capi.phic_request()
+        q.n, q.nnz = self.n, self.nnz
+        if not self.op:
+            q.rowptr, q.colidx, q.values = self.rowptr.data_ptr(), self.colidx.data_ptr(), self.values.data_ptr()
+        q.op = self.op
+        q.V, q.W = self.V.data_ptr(), self.W.data_ptr()
+        q.prec, q.p, q.r = self.prec, self.p, self.r
+        q.flags = capi.PHIC_NO_V0 if self.no_v0 else 0
+        q.tol, q.max_terms = self.tol, self.max_terms
+        for i in range(self.r):
+            q.t[i], q.alpha[i] = float(self.t[i]), float(self.alpha[i])
+        return q
+
+
+class Server:
+    """Continuous-batching request loop (phic_server_*): a worker thread in the library admits requests
+    by device memory and runs them together in batched slices.
+
+        srv = Server(arena_bytes=8 << 30)
+        rid = srv.submit(HostRequest(A, V, t, alpha))
+        info = srv.wait(rid); W = srv.result(rid)
+    """
+
+    def __init__(self, arena_bytes: int = 4 << 30, rows_per_cta: int = 0, blocks_per_sm: int = 0,
+                 max_steps: int = 0, max_active: int = 0, device: int = 0, m: int = 0):
+        self.lib = capi.load()
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=f"cuda:{device}")
+        cfg = capi.phic_server_config(self.arena.data_ptr(), self.arena.numel(), int(rows_per_cta), int(blocks_per_sm),
+                                      int(max_steps), int(max_active), int(device), int(m))
+        h = ctypes.c_void_p(0)
+        capi.check(self.lib.phic_server_create(ctypes.byref(cfg), ctypes.byref(h)), "phic_server_create")
+        self.handle = h
+        self.requests = {}
+
+    def submit(self, req: HostRequest) -> int:
+        rid = ctypes.c_int64(0)
+        q = req.struct()
+        capi.check(self.lib.phic_server_submit(self.handle, ctypes.byref(q), ctypes.byref(rid)), "phic_server_submit")
+        self.requests[rid.value] = req
+        return int(rid.value)
+
+    def add_operator(self, op: HostOperator) -> int:
+        oid = ctypes.c_int64(0)
+        capi.check(self.lib.phic_server_add_operator(self.handle, ctypes.byref(op.struct()), ctypes.byref(oid)),
+                   "phic_server_add_operator")
+        self.requests[oid.value] = op
+        return int(oid.value)
+
+    def operator_params(self, oid: int):
+        ready = ctypes.c_int32(0)
+        prm = capi.phic_params()
+        capi.check(self.lib.phic_server_operator_params(self.handle, int(oid), ctypes.byref(ready), ctypes.byref(prm)),
+                   "phic_server_operator_params")
+        if not ready.value:
+            return None
+        return dict(xi=prm.xi, s=prm.s, s0=prm.s0, f_star=prm.f_star, r=prm.r, evals=prm.evals, status=prm.status)
+
+    def remove_operator(self, oid: int):
+        capi.check(self.lib.phic_server_remove_operator(self.handle, int(oid)), "phic_server_remove_operator")
+
+    def query(self, rid: int) -> dict:
+        info = capi.phic_request_info()
+        capi.check(self.lib.phic_server_query(self.handle, int(rid), ctypes.byref(info)), "phic_server_query")
+        return _info_dict(info)
+
+    def wait(self, rid: int, timeout_ms: float = -1.0) -> dict:
+        info = capi.phic_request_info()
+        capi.check(self.lib.phic_server_wait(self.handle, int(rid), float(timeout_ms), ctypes.byref(info)),
+                   "phic_server_wait")
+        return _info_dict(info)
+
+    def result(self, rid: int) -> torch.Tensor:
+        return self.requests[rid].W
+
+    def counters(self) -> dict:
+        c = capi.phic_server_counters()
+        capi.check(self.lib.phic_server_counters_get(self.handle, ctypes.byref(c)), "phic_server_counters_get")
+        return {k: getattr(c, k) for k, _ in capi.phic_server_counters._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.phic_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

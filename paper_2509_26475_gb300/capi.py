@@ -15,6 +15,7 @@ PHIC_OK, PHIC_INVALID_ARG, PHIC_NONFINITE, PHIC_TERM_CAP, PHIC_TIMEOUT, PHIC_CUD
 PHIC_F64, PHIC_F32 = 0, 1
 PHIC_NO_V0 = 1
 PHIC_PHASE_SERIES, PHIC_PHASE_RECOVER = 0x10, 0x20
+PHIC_BATCH_SELECT, PHIC_BATCH_NO_SOLVE = 0x100, 0x200
 PHIC_MAX_R, PHIC_MAX_P, PHIC_MAX_WIDTH = 16, 15, 128
 PHIC_NOALLOC_MAX_BYTES = 32 << 20
 
@@ -50,6 +51,60 @@ class phic_stats(ctypes.Structure):
                 ("spmm_count", ctypes.c_int64), ("xi", ctypes.c_double), ("s", ctypes.c_double)]
 
 
+class phic_batch_item(ctypes.Structure):
+    _fields_ = [("A", phic_csr), ("p", ctypes.c_int32), ("r", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("max_terms", ctypes.c_int32), ("V", ctypes.c_void_p), ("W", ctypes.c_void_p),
+                ("params", ctypes.c_void_p), ("stats", ctypes.c_void_p), ("v_select", ctypes.c_void_p),
+                ("tol", ctypes.c_double), ("s_hint", ctypes.c_double), ("t", ctypes.c_double * 16),
+                ("alpha", ctypes.c_double * 16)]
+
+
+class phic_batch_config(ctypes.Structure):
+    _fields_ = [("rows_per_cta", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("max_steps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class phic_batch_info(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("count", ctypes.c_int32),
+                ("max_team", ctypes.c_int32), ("entries", ctypes.c_int64), ("est_makespan_us", ctypes.c_double),
+                ("est_busy_frac", ctypes.c_double)]
+
+
+class phic_server_config(ctypes.Structure):
+    _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t), ("rows_per_cta", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("max_steps", ctypes.c_int32), ("max_active", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("m", ctypes.c_int32)]
+
+
+class phic_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("W", ctypes.c_void_p), ("prec", ctypes.c_int32), ("p", ctypes.c_int32), ("r", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("tol", ctypes.c_double), ("max_terms", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("op", ctypes.c_int64), ("t", ctypes.c_double * 16),
+                ("alpha", ctypes.c_double * 16)]
+
+
+class phic_operator(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p), ("prec", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class phic_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("submit_ns", ctypes.c_int64),
+                ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64), ("slices", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("params", phic_params), ("stats", phic_stats)]
+
+
+class phic_server_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("slices", ctypes.c_int64), ("max_slice_requests", ctypes.c_int64),
+                ("arena_in_use", ctypes.c_int64), ("arena_peak", ctypes.c_int64), ("gpu_busy_ms", ctypes.c_double)]
+
+
+PHIC_REQ_QUEUED, PHIC_REQ_LOADING, PHIC_REQ_RUNNING, PHIC_REQ_COPYING, PHIC_REQ_DONE = range(5)
+
 _lock = threading.Lock()
 _lib = None
 
@@ -69,6 +124,34 @@ SIGNATURES = [
     ("phic_solve_noalloc", ctypes.c_int, [ctypes.POINTER(phic_csr), ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
                                           ctypes.c_double, _P, ctypes.c_uint32, ctypes.c_int32, _P, _P,
                                           ctypes.c_int32, _P]),
+    ("phic_batch_workspace_size", ctypes.c_int, [ctypes.POINTER(phic_batch_item), ctypes.c_int32,
+                                                 ctypes.POINTER(phic_select_opts), ctypes.POINTER(ctypes.c_size_t)]),
+    ("phic_batch_create", ctypes.c_int, [ctypes.POINTER(phic_batch_item), ctypes.c_int32,
+                                         ctypes.POINTER(phic_select_opts), ctypes.POINTER(phic_batch_config), _P,
+                                         ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_void_p)]),
+    ("phic_batch_launch", ctypes.c_int, [_P, _P]),
+    ("phic_batch_resume", ctypes.c_int, [_P, _P]),
+    ("phic_batch_pending", ctypes.c_int, [_P, _P, _P]),
+    ("phic_batch_info_get", ctypes.c_int, [_P, ctypes.POINTER(phic_batch_info)]),
+    ("phic_batch_destroy", None, [_P]),
+    ("phic_batch_plan_host", ctypes.c_int, [ctypes.POINTER(phic_batch_item), ctypes.c_int32,
+                                            ctypes.POINTER(phic_select_opts), ctypes.POINTER(phic_batch_config),
+                                            ctypes.c_int32, _P, _P, _P, ctypes.c_int64,
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
+    ("phic_batch_autotune", ctypes.c_int, [ctypes.POINTER(phic_batch_item), ctypes.c_int32,
+                                           ctypes.POINTER(phic_select_opts), _P, ctypes.c_size_t,
+                                           ctypes.POINTER(phic_batch_config), ctypes.c_int32, ctypes.c_int32, _P,
+                                           ctypes.POINTER(phic_batch_config), ctypes.POINTER(ctypes.c_double)]),
+    ("phic_server_create", ctypes.c_int, [ctypes.POINTER(phic_server_config), ctypes.POINTER(ctypes.c_void_p)]),
+    ("phic_server_submit", ctypes.c_int, [_P, ctypes.POINTER(phic_request), ctypes.POINTER(ctypes.c_int64)]),
+    ("phic_server_add_operator", ctypes.c_int, [_P, ctypes.POINTER(phic_operator), ctypes.POINTER(ctypes.c_int64)]),
+    ("phic_server_operator_params", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                                   ctypes.POINTER(phic_params)]),
+    ("phic_server_remove_operator", ctypes.c_int, [_P, ctypes.c_int64]),
+    ("phic_server_query", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(phic_request_info)]),
+    ("phic_server_wait", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(phic_request_info)]),
+    ("phic_server_counters_get", ctypes.c_int, [_P, ctypes.POINTER(phic_server_counters)]),
+    ("phic_server_destroy", None, [_P]),
     ("phic_set_spin_limit_ms", None, [ctypes.c_double]),
     ("phic_set_blocks_per_sm", None, [ctypes.c_int32]),
     ("phic_set_test_fault", None, [ctypes.c_int32]),

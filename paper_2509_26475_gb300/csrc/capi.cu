@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "layout.h"
 #include "phicomb.h"
 
 namespace phic {
@@ -17,62 +18,11 @@ std::atomic<long long> g_spin_ns{2000000000LL};
 std::atomic<int> g_blocks_per_sm{0};
 std::atomic<int> g_fault{0};
 
-constexpr size_t kAlign = 256;
-size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-
-bool aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) % kAlign) == 0; }
-
-bool csr_ok(const phic_csr* A) {
-  if (!A) return false;
-  if (A->n < 1 || A->n >= (int64_t)INT32_MAX || A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX) return false;
-  if (!A->rowptr) return false;
-  if (A->nnz > 0 && (!A->colidx || !A->values)) return false;
-  if (A->prec != PHIC_F64 && A->prec != PHIC_F32) return false;
-  return true;
-}
-
-struct SelectLayout {
-  size_t ctl, part, basis, total;
-};
-SelectLayout select_layout(int64_t n, int m) {
-  SelectLayout L;
-  L.ctl = 0;
-  L.part = align_up(sizeof(Ctl));
-  L.basis = L.part + align_up((size_t)2 * max_select_grid() * 16);
-  L.total = L.basis + align_up((size_t)n * (size_t)((m + 2) / 2 * 2) * sizeof(double));  // pairs of vectors
-  return L;
-}
-
-struct SolveLayout {
-  size_t ctlS, ctlR, state, A1, rowflag, Vt[2], Dt[2], S, Ft[2], E, total;
-  TileLayout sl, fl;
-};
-SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec) {
-  SolveLayout L;
-  const size_t es = prec == PHIC_F32 ? 4 : 8;
-  L.sl = pick_layout((p + 1) * r, (int)es);
-  L.fl = pick_layout(p == 0 ? r : 2 * r, (int)es);
-  const size_t tileS = align_up((size_t)n * L.sl.ws * es);
-  const size_t tileF = align_up((size_t)n * L.fl.ws * es);
-  size_t off = 0;
-  L.ctlS = off; off += align_up(sizeof(Ctl));
-  L.ctlR = off; off += align_up(sizeof(Ctl));
-  L.state = off; off += align_up(sizeof(SolveState));
-  const size_t head = off;  // control blocks and state: zeroed before each solve
-  L.A1 = off; off += align_up((size_t)(nnz > 0 ? nnz : 1) * 2 * es);  // (column, value) entries
-  L.rowflag = off; off += align_up((size_t)n);
-  for (int q = 0; q < 2; ++q) { L.Vt[q] = off; off += tileS; }
-  for (int q = 0; q < 2; ++q) { L.Dt[q] = off; off += tileS; }
-  L.S = off; off += tileS;
-  for (int q = 0; q < 2; ++q) { L.Ft[q] = off; off += tileF; }
-  L.E = off; off += tileF;
-  L.total = off;
-  (void)head;
-  return L;
-}
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+unsigned long long spin_limit_ns() { return (unsigned long long)g_spin_ns.load(); }
 
 int blocks_per_sm(int elem_bytes) {
   (void)elem_bytes;
@@ -107,33 +57,14 @@ phic_status phic_select_params(const phic_csr* A, const phic_select_opts* opts, 
   phic_select_opts o;
   if (opts) o = *opts; else phic_select_opts_default(&o);
   if (!csr_ok(A) || !params_dev || !ws || !aligned(ws)) return PHIC_INVALID_ARG;
-  if (o.m < 1 || o.m > 128 || !(o.tol > 0.0) || !std::isfinite(o.tol) || !(o.delta > 0.0) || !(o.delta <= 1.0) ||
-      o.max_evals < 1 || !(o.spin_limit_ms > 0.0))
-    return PHIC_INVALID_ARG;
+  if (!select_opts_ok(o)) return PHIC_INVALID_ARG;
   const SelectLayout L = select_layout(A->n, o.m);
   if (ws_bytes < L.total) return PHIC_WORKSPACE_TOO_SMALL;
   char* base = static_cast<char*>(ws);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(base + L.ctl, 0, sizeof(Ctl), st) != cudaSuccess) return PHIC_CUDA_ERROR;
   SelectArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.n = (int)A->n;
-  a.nnz = (int)A->nnz;
-  a.rowptr = A->rowptr;
-  a.colidx = A->colidx;
-  a.vals = A->values;
-  a.vals_f32 = A->prec == PHIC_F32;
-  a.v = v;
-  a.seed = o.seed;
-  a.m = o.m;
-  a.tol = o.tol;
-  a.delta = o.delta;
-  a.max_evals = o.max_evals;
-  a.Vb = reinterpret_cast<double*>(base + L.basis);
-  a.part = base + L.part;
-  a.ctl = reinterpret_cast<Ctl*>(base + L.ctl);
-  a.out = params_dev;
-  a.spin_ns = (unsigned long long)(o.spin_limit_ms * 1e6);
+  fill_select_args(a, A, o, v, base, L, params_dev);
   return launch_select(a, st, nullptr) == cudaSuccess ? PHIC_OK : PHIC_CUDA_ERROR;
 }
 
@@ -154,59 +85,22 @@ phic_status phic_solve_workspace_size(int64_t n, int64_t nnz, int32_t p, int32_t
 phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, const double* t, const double* alpha,
                        double tol, const phic_params* params_dev, uint32_t flags, int32_t max_terms, void* W, void* ws,
                        size_t ws_bytes, phic_stats* stats_dev, int32_t prec, phic_stream_t stream) {
-  if (!csr_ok(A) || A->prec != prec || !V || !W || !t || !alpha || !params_dev || !ws || !aligned(ws))
-    return PHIC_INVALID_ARG;
-  if (p < 0 || p > PHIC_MAX_P || r < 1 || r > PHIC_MAX_R || (p + 1) * r > PHIC_MAX_WIDTH) return PHIC_INVALID_ARG;
-  if (!(tol > 0.0) || !std::isfinite(tol)) return PHIC_INVALID_ARG;
-  if ((flags & ~(PHIC_NO_V0 | PHIC_PHASE_SERIES | PHIC_PHASE_RECOVER)) != 0 || ((flags & PHIC_NO_V0) && p == 0))
+  if (!solve_args_ok(A, p, r, V, t, alpha, tol, flags, PHIC_NO_V0 | PHIC_PHASE_SERIES | PHIC_PHASE_RECOVER, prec) ||
+      !W || !params_dev || !ws || !aligned(ws))
     return PHIC_INVALID_ARG;
   bool run_series = true, run_recover = true;
   if (flags & (PHIC_PHASE_SERIES | PHIC_PHASE_RECOVER)) {
     run_series = (flags & PHIC_PHASE_SERIES) != 0;
     run_recover = (flags & PHIC_PHASE_RECOVER) != 0;
   }
-  for (int i = 0; i < r; ++i)
-    if (!std::isfinite(t[i]) || !std::isfinite(alpha[i])) return PHIC_INVALID_ARG;
   const SolveLayout L = solve_layout(A->n, A->nnz, p, r, prec);
   if (ws_bytes < L.total) return PHIC_WORKSPACE_TOO_SMALL;
   char* base = static_cast<char*>(ws);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (run_series && cudaMemsetAsync(base, 0, L.A1, st) != cudaSuccess) return PHIC_CUDA_ERROR;  // control + state
   SolveArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.n = (int)A->n;
-  a.nnz = (int)A->nnz;
-  a.rowptr = A->rowptr;
-  a.colidx = A->colidx;
-  a.vals = A->values;
-  a.A1 = base + L.A1;
-  a.rowflag = reinterpret_cast<unsigned char*>(base + L.rowflag);
-  a.Vin = V;
-  a.W = W;
-  a.p = p;
-  a.r = r;
-  a.no_v0 = (flags & PHIC_NO_V0) ? 1 : 0;
-  a.S_lay = L.sl;
-  a.F_lay = L.fl;
-  for (int i = 0; i < r; ++i) {
-    a.t[i] = t[i];
-    a.alpha[i] = alpha[i];
-  }
-  a.tol = tol;
-  a.max_terms = max_terms > 0 ? max_terms : 610;
-  a.params = params_dev;
-  for (int q = 0; q < 2; ++q) {
-    a.Vt[q] = base + L.Vt[q];
-    a.Dt[q] = base + L.Dt[q];
-    a.Ft[q] = base + L.Ft[q];
-  }
-  a.S = base + L.S;
-  a.E = base + L.E;
-  a.ctlS = reinterpret_cast<Ctl*>(base + L.ctlS);
-  a.ctlR = reinterpret_cast<Ctl*>(base + L.ctlR);
-  a.state = reinterpret_cast<SolveState*>(base + L.state);
-  a.stats = stats_dev;
-  a.spin_ns = (unsigned long long)g_spin_ns.load();
+  fill_solve_args(a, A, p, r, V, t, alpha, tol, params_dev, flags, max_terms, W, base, L, stats_dev,
+                  (unsigned long long)g_spin_ns.load());
   a.fault = g_fault.exchange(0);
   if (run_series && launch_series(a, prec, st, nullptr) != cudaSuccess) return PHIC_CUDA_ERROR;
   if (run_recover && launch_recover(a, prec, st, nullptr) != cudaSuccess) return PHIC_CUDA_ERROR;
@@ -274,12 +168,7 @@ extern "C" phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t 
                                           const double* alpha, double tol, const phic_params* params_dev,
                                           uint32_t flags, int32_t max_terms, void* W, phic_stats* stats_dev,
                                           int32_t prec, phic_stream_t stream) {
-  if (!csr_ok(A) || A->prec != prec || !V || !W || !t || !alpha || !params_dev) return PHIC_INVALID_ARG;
-  if (p < 0 || p > PHIC_MAX_P || r < 1 || r > PHIC_MAX_R || (p + 1) * r > PHIC_MAX_WIDTH) return PHIC_INVALID_ARG;
-  if (!(tol > 0.0) || !std::isfinite(tol)) return PHIC_INVALID_ARG;
-  if ((flags & ~PHIC_NO_V0) != 0 || ((flags & PHIC_NO_V0) && p == 0)) return PHIC_INVALID_ARG;
-  for (int i = 0; i < r; ++i)
-    if (!std::isfinite(t[i]) || !std::isfinite(alpha[i])) return PHIC_INVALID_ARG;
+  if (!solve_args_ok(A, p, r, V, t, alpha, tol, flags, PHIC_NO_V0, prec) || !W || !params_dev) return PHIC_INVALID_ARG;
   const SolveLayout L = solve_layout(A->n, A->nnz, p, r, prec);
   if (L.total > (size_t)PHIC_NOALLOC_MAX_BYTES) return PHIC_WORKSPACE_TOO_SMALL;
   void* scratch = nullptr;
@@ -289,41 +178,8 @@ extern "C" phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t 
   // control blocks and loop state must start at zero; the tiles are written before they are read
   if (cudaMemsetAsync(base, 0, L.A1, st) != cudaSuccess) return PHIC_CUDA_ERROR;
   SolveArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.n = (int)A->n;
-  a.nnz = (int)A->nnz;
-  a.rowptr = A->rowptr;
-  a.colidx = A->colidx;
-  a.vals = A->values;
-  a.A1 = base + L.A1;
-  a.rowflag = reinterpret_cast<unsigned char*>(base + L.rowflag);
-  a.Vin = V;
-  a.W = W;
-  a.p = p;
-  a.r = r;
-  a.no_v0 = (flags & PHIC_NO_V0) ? 1 : 0;
-  a.S_lay = L.sl;
-  a.F_lay = L.fl;
-  for (int i = 0; i < r; ++i) {
-    a.t[i] = t[i];
-    a.alpha[i] = alpha[i];
-  }
-  a.tol = tol;
-  a.max_terms = max_terms > 0 ? max_terms : 610;
-  a.params = params_dev;
-  for (int q = 0; q < 2; ++q) {
-    a.Vt[q] = base + L.Vt[q];
-    a.Dt[q] = base + L.Dt[q];
-    a.Ft[q] = base + L.Ft[q];
-  }
-  a.S = base + L.S;
-  a.E = base + L.E;
-  a.ctlS = reinterpret_cast<Ctl*>(base + L.ctlS);
-  a.ctlR = reinterpret_cast<Ctl*>(base + L.ctlR);
-  a.state = reinterpret_cast<SolveState*>(base + L.state);
-  a.stats = stats_dev;
-  a.spin_ns = (unsigned long long)g_spin_ns.load();
-  a.fault = 0;
+  fill_solve_args(a, A, p, r, V, t, alpha, tol, params_dev, flags, max_terms, W, base, L, stats_dev,
+                  (unsigned long long)g_spin_ns.load());
   if (launch_series(a, prec, st, nullptr) != cudaSuccess) return PHIC_CUDA_ERROR;
   if (launch_recover(a, prec, st, nullptr) != cudaSuccess) return PHIC_CUDA_ERROR;
   return PHIC_OK;

@@ -78,6 +78,12 @@ struct SolveArgs {
   int fault;
 };
 
+// Rows per chunk of Algorithm 1's sums of squares (each chunk's partial is one 16-byte record).
+constexpr int kSelectChunk = 1024;
+inline size_t select_partials_bytes(long long n) {
+  return (size_t)2 * (size_t)((n + kSelectChunk - 1) / kSelectChunk) * 16;
+}
+
 struct SelectArgs {
   int n, nnz;
   const int* rowptr;
@@ -90,7 +96,7 @@ struct SelectArgs {
   double tol, delta;
   int max_evals;
   double* Vb;    // basis V_0..V_m, pair-interleaved: V_k[row] at ((k/2) n + row) 2 + k%2
-  void* part;    // 2 x grid scaled sums of squares
+  void* part;    // 2 x ceil(n / kSelectChunk) scaled sums of squares
   Ctl* ctl;
   phic_params* out;
   unsigned long long spin_ns;
@@ -99,7 +105,7 @@ struct SelectArgs {
 // One instance of a batched launch: its solve and selection arguments (both pointing at the instance's
 // control block for this launch) and the phases to run.
 constexpr int kPhaseSelect = 1, kPhaseSeries = 2, kPhaseRecover = 4;
-struct BatchInst {
+struct alignas(16) BatchInst {
   SolveArgs sa;
   SelectArgs sel;
   int phases;     // kPhase* bits
@@ -131,6 +137,14 @@ cudaError_t launch_params_set(phic_params* p, double xi, double s, cudaStream_t 
 int max_select_grid();
 void count_launch();
 int blocks_per_sm(int elem_bytes);
+// Bound on one barrier wait (ns) set by phic_set_spin_limit_ms.
+unsigned long long spin_limit_ns();
+// Enqueues a one-block kernel that writes the number of unfinished solves of the batch to *out.
+cudaError_t launch_batch_pending(const BatchInst* inst, int count, int* out, cudaStream_t st);
+// Enqueues a kernel that copies, for each instance of a slice, its done flag, phic_stats and
+// phic_params into contiguous device arrays (for one small read-back).
+cudaError_t launch_batch_collect(const BatchInst* inst, int count, int* done, phic_stats* stats, phic_params* params,
+                                 cudaStream_t st);
 // Batched launch with `grid` CTAs of the kernel built for `minb` (2 or 3) resident blocks per SM.
 cudaError_t launch_batch(const BatchArgs& b, int grid, int minb, cudaStream_t st);
 // Resident blocks per SM of the batched kernel built for minb (0 on error).

@@ -36,7 +36,7 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t st, int* grid_out) {
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   if (per_sm > 2) per_sm = 2;  // short passes: fewer blocks make the fixed-order combine and barrier cheaper
-  long long need = ((long long)a.n + kBlock - 1) / kBlock;
+  long long need = ((long long)a.n + kSelectChunk - 1) / kSelectChunk;  // the summed passes go by chunks
   long long grid = (long long)sms * per_sm;
   if (need < grid) grid = need < 1 ? 1 : need;
   if (grid > max_select_grid()) grid = max_select_grid();

@@ -11,10 +11,10 @@
 //   4. Brent's minimiser of f(xi) = ||sum_k binom(m,k) (-xi/s0)^(m-k) V_k||_2^(1/m) on
 //      [-sqrt(n) s0, sqrt(n) s0], each evaluation one pass over the basis;
 //   5. s = s0 f(xi*) / (tol m!)^(1/m).
-// 2-norms are sums of squares scaled by powers of two (exact scalings), combined per block and then
-// across the team's blocks in a fixed order, so every block derives bit-identical L_k and f values and
-// takes the same branches (the rounding of these sums depends on the team size).  Brent's scalar logic
-// runs in thread 0 of every block.
+// 2-norms are sums of squares scaled by powers of two (exact scalings), formed per fixed chunk of rows and
+// combined in a fixed order, so every block derives bit-identical L_k and f values and takes the same
+// branches, and the outcome does not depend on how many CTAs run it.  Brent's scalar logic runs in
+// thread 0 of every block.
 #include <float.h>
 #include <math.h>
 
@@ -122,34 +122,44 @@ struct SelShared {
   BrentSM br;
 };
 
-// Writes this member's partial to part[parity][rank] (thread 0 holds the block total).
-__device__ __forceinline__ void put_partial(Ssq* part, int parity, Ssq blk, const Team& tm) {
-  if (threadIdx.x == 0) part[(size_t)parity * tm.size + tm.rank] = blk;
+// Sums of squares over the rows are formed per fixed chunk of kChunk rows (thread t adds rows
+// c kChunk + u kBlock + t, u ascending, then the block's fixed tree), and the chunks' partials are combined
+// in a fixed order by every member: the result, and every decision taken on it, is the same for any team
+// size.
+constexpr int kChunk = kSelectChunk;
+static_assert(kChunk % kBlock == 0, "a chunk is a whole number of block-wide row sweeps");
+
+__device__ __forceinline__ int chunk_count(int n) { return (n + kChunk - 1) / kChunk; }
+
+// Calls y = f(row) for every row of this member's chunks and stores each chunk's scaled sum of squares
+// of y in part[parity][chunk].
+template <typename F>
+__device__ __forceinline__ void chunk_pass(int n, const Team& tm, Ssq* part, int parity, F&& f) {
+  const int nch = chunk_count(n);
+  for (int c = tm.rank; c < nch; c += tm.size) {
+    Ssq acc = ssq_empty();
+#pragma unroll
+    for (int u = 0; u < kChunk / kBlock; ++u) {
+      const long long row = (long long)c * kChunk + u * kBlock + threadIdx.x;
+      if (row < n) ssq_add(acc, f(row));
+    }
+    const Ssq blk = block_ssq(acc);
+    if (threadIdx.x == 0) part[(size_t)parity * nch + c] = blk;
+  }
 }
 
-// Combines all members' partials in a fixed order; the result is valid in thread 0.  Each lane of warp
-// 0 issues its loads (up to 8 at a time) before combining, so the L2 latencies overlap.
-__device__ __forceinline__ Ssq gather_partials(const Ssq* part, int parity, int size) {
+// Total of all chunks' partials in a fixed order; valid in thread 0.
+__device__ __forceinline__ Ssq gather_chunks(const Ssq* part, int parity, int n) {
+  const int nch = chunk_count(n);
+  const volatile Ssq* pp = part + (size_t)parity * nch;
   Ssq acc = ssq_empty();
-  if (threadIdx.x < 32) {
-    const volatile Ssq* pp = part + (size_t)parity * size;
-    for (int b0 = threadIdx.x; b0 < size; b0 += 32 * 8) {
-      Ssq x[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int b = b0 + 32 * u;
-        x[u] = ssq_empty();
-        if (b < size) {
-          x[u].e = pp[b].e;
-          x[u].ssq = pp[b].ssq;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc = ssq_combine(acc, x[u]);
-    }
-    acc = warp_ssq(acc);
+  for (int c = threadIdx.x; c < nch; c += kBlock) {
+    Ssq x;
+    x.e = pp[c].e;
+    x.ssq = pp[c].ssq;
+    acc = ssq_combine(acc, x);
   }
-  return acc;
+  return block_ssq(acc);
 }
 
 // The basis is stored in interleaved pairs: V_k[row] at ((k/2) n + row) 2 + k%2, so that an objective
@@ -174,7 +184,7 @@ __device__ __forceinline__ double spmv_row(const SelectArgs& a, const VT* __rest
 
 }  // namespace
 
-// Algorithm 1 on the team tm; a.part holds 2 x tm.size partials and a.ctl is tm.ctl.
+// Algorithm 1 on the team tm; a.part holds 2 x ceil(n / kChunk) partials and a.ctl is tm.ctl.
 template <typename VT>
 __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelShared& sh) {
   Ctl* ctl = tm.ctl;
@@ -199,8 +209,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
   // ---- v (given or drawn), its 2-norm; CSR structure check ------------------------------------------
   double* V0 = a.Vb;
   {
-    Ssq acc = ssq_empty();
-    for (long long row = first; row < n; row += stride) {
+    chunk_pass(n, tm, part, pc & 1, [&](long long row) {
       const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
       if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) bad = 1;
       double x;
@@ -211,13 +220,11 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
         x = 2.0 * u - 1.0;
       }
       V0[vidx(0, n, row)] = x;
-      ssq_add(acc, x);
-    }
-    const Ssq blk = block_ssq(acc);
-    put_partial(part, pc & 1, blk, tm);
+      return x;
+    });
     if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(ctl, PHIC_INVALID_ARG);
     if (!team_sync(tm)) return;
-    const Ssq tot = gather_partials(part, pc & 1, tm.size);
+    const Ssq tot = gather_chunks(part, pc & 1, n);
     ++pc;
     if (threadIdx.x == 0) {
       const double lg = ssq_log_norm(tot);
@@ -236,17 +243,14 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
   }
   // ---- V_0 = v / ||v|| and L_0 ------------------------------------------------------------------------
   {
-    Ssq acc = ssq_empty();
     const double nv = sh.nv;
-    for (long long row = first; row < n; row += stride) {
+    chunk_pass(n, tm, part, pc & 1, [&](long long row) {
       const double x = V0[vidx(0, n, row)] / nv;
       V0[vidx(0, n, row)] = x;
-      ssq_add(acc, x);
-    }
-    const Ssq blk = block_ssq(acc);
-    put_partial(part, pc & 1, blk, tm);
+      return x;
+    });
     if (!team_sync(tm)) return;
-    const Ssq tot = gather_partials(part, pc & 1, tm.size);
+    const Ssq tot = gather_chunks(part, pc & 1, n);
     ++pc;
     if (threadIdx.x == 0) {
       sh.L[0] = ssq_log_norm(tot);
@@ -258,17 +262,14 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
   // ---- guarded power basis ----------------------------------------------------------------------------
   for (int k = 1; k <= m && sh.go; ++k) {
     const double* __restrict__ Vp = a.Vb + vidx(k - 1, n, 0);
-    Ssq acc = ssq_empty();
-    for (long long row = first; row < n; row += stride) {
+    chunk_pass(n, tm, part, pc & 1, [&](long long row) {
       const double y = spmv_row<VT>(a, vals, Vp, (int)row, bad);
       a.Vb[vidx(k, n, row)] = y;
-      ssq_add(acc, y);
-    }
-    const Ssq blk = block_ssq(acc);
-    put_partial(part, pc & 1, blk, tm);
+      return y;
+    });
     if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(ctl, PHIC_INVALID_ARG);
     if (!team_sync(tm)) return;
-    const Ssq tot = gather_partials(part, pc & 1, tm.size);
+    const Ssq tot = gather_chunks(part, pc & 1, n);
     ++pc;
     if (threadIdx.x == 0) {
       const double Lk = ssq_log_norm(tot);
@@ -348,10 +349,9 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
       sh.coef[kk] = sh.binom[kk] * pow(z, (double)(m - kk));
     }
     __syncthreads();
-    Ssq acc = ssq_empty();
     const double2* __restrict__ Vp2 = reinterpret_cast<const double2*>(a.Vb);
     const int pairs = (m + 1) >> 1;
-    for (long long row = first; row < n; row += stride) {
+    chunk_pass(n, tm, part, pc & 1, [&](long long row) {
       double y = 0.0;
       for (int jj = 0; jj < pairs; ++jj) {  // y = sum_k coef_k V_k[row], k ascending
         const double2 v = Vp2[(size_t)jj * n + row];
@@ -359,12 +359,10 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
         y = fma(sh.coef[2 * jj + 1], v.y, y);
       }
       if ((m + 1) & 1) y = fma(sh.coef[m], a.Vb[vidx(m, n, row)], y);
-      ssq_add(acc, y);
-    }
-    const Ssq blk = block_ssq(acc);
-    put_partial(part, pc & 1, blk, tm);
+      return y;
+    });
     if (!team_sync(tm)) return;
-    const Ssq tot = gather_partials(part, pc & 1, tm.size);
+    const Ssq tot = gather_chunks(part, pc & 1, n);
     ++pc;
     if (threadIdx.x == 0) {
       const double lg = ssq_log_norm(tot);

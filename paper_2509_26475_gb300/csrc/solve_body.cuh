@@ -289,7 +289,7 @@ struct RecoverScalars {
   float fcoef[PHIC_MAX_R];
   T cj[PHIC_MAX_P + 1][PHIC_MAX_R];
   int s_int, series_terms, status, eA, nodiag;
-  int rec_init, j_done, cur;
+  int done, rec_init, j_done, cur;
   double cF0;
 };
 
@@ -514,6 +514,9 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   // ---- k >= 2:  V <- V Jsh;  D <- A_1 D (I kron T/s) + V;  S <- S + D/k!  (divided by k!) ----------
   const T xiB = (T)(-sc.xi * ldexp(1.0, -sc.eA));  // explicit shift for rows without a stored diagonal
   const bool nodiag = sc.nodiag != 0;
+  // argument fields used per row, kept in registers (the argument block may live in shared memory)
+  const int* __restrict__ rowptr = a.rowptr;
+  const unsigned char* __restrict__ rowflag = a.rowflag;
   while (lc.go) {
     const int kk = lc.k;
     const int ph = phase++;
@@ -542,8 +545,8 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
         T acc[CW];
 #pragma unroll
         for (int j = 0; j < CW; ++j) acc[j] = T(0);
-        spmm_ent<T, CW>(a.rowptr, ent, Do, L.ws, c0, row, acc);
-        if (nodiag && a.rowflag[row]) {  // no stored diagonal: apply the shift explicitly
+        spmm_ent<T, CW>(rowptr, ent, Do, L.ws, c0, row, acc);
+        if (nodiag && rowflag[row]) {  // no stored diagonal: apply the shift explicitly
           T own[CW];
           VecIO<T, CW>::ld(Do + o, own);
 #pragma unroll
@@ -656,6 +659,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
     sc.xi = vs->xi;
     sc.eA = vs->eA;
     sc.nodiag = vs->nodiag;
+    sc.done = vs->done;
     sc.rec_init = vs->rec_init;
     sc.j_done = vs->j_done;
     sc.cur = vs->cur;
@@ -669,6 +673,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
     }
   }
   __syncthreads();
+  if (sc.done) return 1;  // finished in an earlier launch
   const bool leader = tm.rank == 0 && threadIdx.x == 0;
   long long rec_terms = 0;  // the leader keeps the counts
   int max_inner = 0;
@@ -784,13 +789,18 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   __syncthreads();
   const T xiB = (T)(-sc.xi * ldexp(1.0, -sc.eA));
   const bool nodiag = sc.nodiag != 0;
+  // argument fields used per row, kept in registers (the argument block may live in shared memory)
+  const int* __restrict__ rowptr = a.rowptr;
+  const unsigned char* __restrict__ rowflag = a.rowflag;
+  const double tol = a.tol;
+  const int max_terms = a.max_terms;
 
   // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||: next term
   auto decide = [&]() {
     int go = 0;
     if (status == PHIC_OK && (!isfinite(c2) || !isfinite(nE))) status = PHIC_NONFINITE;
-    if (status == PHIC_OK && c1 + c2 > a.tol * nE) {
-      if (k >= a.max_terms) status = PHIC_TERM_CAP;
+    if (status == PHIC_OK && c1 + c2 > tol * nE) {
+      if (k >= max_terms) status = PHIC_TERM_CAP;
       else {
         k += 1;
         c1 = c2;
@@ -851,7 +861,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
           act[u] = it < br.padded && row[u] < br.r1 && lane < L.L;
         }
         T acc[NR][CW];
-        spmm_rows<T, CW, NR>(a.rowptr, ent, Go, L.ws, c0, row, act, acc);
+        spmm_rows<T, CW, NR>(rowptr, ent, Go, L.ws, c0, row, act, acc);
         float pF[NR], pE[NR];
 #pragma unroll
         for (int u = 0; u < NR; ++u) {
@@ -859,7 +869,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
           pE[u] = 0.f;
           if (act[u]) {
             const size_t o = (size_t)row[u] * L.ws + c0;
-            const bool shift_row = nodiag && a.rowflag[row[u]];
+            const bool shift_row = nodiag && rowflag[row[u]];
             T e[CW];
             if (kk == 1 || shift_row) {
               T own[CW];

@@ -191,3 +191,86 @@ def workload_advdiff2d_1024(h: float, tol: float):
     A = convection_diffusion(1024, 2, 1e3)
     return dict(name=f"advdiff2d-1024^2-Pe1e3-p4-r4-h{h:g}", A=A, V=random_vectors(4, A.n, 3),
                 t=np.array([0.25, 0.5, 0.75, 1.0]) * h, alpha=np.ones(4), tol=tol)
+
+
+# ---- many uneven instances (batched launches) -------------------------------------------------------
+def shifted_laplacian(shape, shift: np.ndarray) -> CSR:
+    """Dirichlet Laplacian on a grid of the given shape (h_d = 1/(shape_d + 1) per axis, scaled by
+    1/h_d^2) plus diag(shift)."""
+    cd = [float(s + 1) ** 2 for s in shape]
+    A = _grid_operator(shape, -2.0 * sum(cd), cd, cd)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    diag = A.colidx == rows
+    vals = A.values.copy()
+    vals[diag] += np.asarray(shift, dtype=np.float64)[rows[diag]]
+    return CSR(A.n, A.rowptr, A.colidx, vals)
+
+
+def batch_instance(seed: int, i: int, n_lo: int = 1000, n_hi: int = 256000, precision: str = "mixed") -> dict:
+    """Instance i of the batching workload: n log-uniform in [n_lo, n_hi] (2-D or 3-D grid, equally
+    likely), a Dirichlet Laplacian plus diagonal shifts U[-10, 0], p in 1..4, r in 1..3, v_j ~ N(0, 1),
+    t_i = tau (i / r) / rho with rho = 4 sum_d 1/h_d^2 + 10 (a Gershgorin bound of |A|) and tau
+    log-uniform in [1, 100], alpha_i ~ U[0.5, 1.5].  precision "mixed" draws FP64 (tol 2^-53) or FP32
+    (tol 2^-24) with equal odds; "f64" / "f32" fix it."""
+    rng = np.random.default_rng([int(seed), int(i)])
+    n_target = float(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+    dim = int(rng.integers(2, 4))
+    if dim == 2:
+        nx = max(2, int(round(np.sqrt(n_target))))
+        shape = (nx, max(2, int(round(n_target / nx))))
+    else:
+        nx = max(2, int(round(n_target ** (1.0 / 3.0))))
+        shape = (nx, nx, max(2, int(round(n_target / (nx * nx)))))
+    n = int(np.prod(shape))
+    shift = rng.uniform(-10.0, 0.0, size=n)
+    p = int(rng.integers(1, 5))
+    r = int(rng.integers(1, 4))
+    rho = 4.0 * sum(float(s + 1) ** 2 for s in shape) + 10.0
+    tau = float(np.exp(rng.uniform(0.0, np.log(100.0))))
+    t = tau * np.arange(1, r + 1) / r / rho
+    alpha = rng.uniform(0.5, 1.5, size=r)
+    f32 = bool(rng.integers(0, 2)) if precision == "mixed" else precision == "f32"
+    V = rng.standard_normal((p + 1, n))
+    return dict(name=f"batch{seed}-{i}", A=shifted_laplacian(shape, shift), V=V, t=t, alpha=alpha, p=p, r=r,
+                prec="f32" if f32 else "f64", tol=2.0**-24 if f32 else 2.0**-53, shape=shape)
+
+
+def workload_batch(count: int = 512, seed: int = 4, precision: str = "mixed", n_lo: int = 1000,
+                   n_hi: int = 256000) -> list:
+    """The batching workload: `count` independent instances (see batch_instance)."""
+    return [batch_instance(seed, i, n_lo, n_hi, precision) for i in range(count)]
+
+
+# ---- the paper's ADR problem (Section 6, fourth experiment) ----------------------------------------
+ADR_EPS, ADR_ALPHA, ADR_GAMMA = 1e-3, -0.5, 1000.0
+
+
+def adr_operator(N: int = 100, eps: float = ADR_EPS, alpha: float = ADR_ALPHA) -> CSR:
+    """A = eps Laplacian - alpha (d/dx + d/dy) on [0,1]^2 with N nodes per direction: nodes
+    x_i = i / N, i = 0..N-1 (spacing 1/N); homogeneous Neumann at x = 0 and y = 0 (ghost value
+    u_{-1} = u_1), homogeneous Dirichlet at x = 1 and y = 1 (node N is the boundary, u = 0); second-order
+    central differences for both terms; x fastest.  n = N^2 (10^4 for N = 100)."""
+    import scipy.sparse as sp
+
+    dx = 1.0 / N
+    main = np.full(N, -2.0 / dx**2)
+    lo = np.full(N - 1, 1.0 / dx**2)
+    up = np.full(N - 1, 1.0 / dx**2)
+    up[0] = 2.0 / dx**2  # Neumann ghost at node 0: u_{-1} = u_1
+    L1 = sp.diags([lo, main, up], [-1, 0, 1], format="csr")
+    dlo = np.full(N - 1, -1.0 / (2 * dx))
+    dup = np.full(N - 1, 1.0 / (2 * dx))
+    dup[0] = 0.0  # (u_1 - u_{-1}) / (2 dx) = 0 at the Neumann node
+    D1 = sp.diags([dlo, dup], [-1, 1], format="csr")
+    I = sp.identity(N, format="csr")
+    A = eps * (sp.kron(I, L1) + sp.kron(L1, I)) - alpha * (sp.kron(I, D1) + sp.kron(D1, I))
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    return from_scipy(A)
+
+
+def adr_initial(N: int = 100) -> np.ndarray:
+    """u(0, x, y) = 256 x^2 y^2 (1-x)^2 (1-y)^2 on the nodes of adr_operator."""
+    x = np.arange(N) / N
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    return (256.0 * X**2 * Y**2 * (1 - X) ** 2 * (1 - Y) ** 2).ravel()
