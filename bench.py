@@ -51,6 +51,11 @@ WORKLOAD_NAME = WORKLOADS[WORKLOAD]["name"] + " tol=2^-53"
 def configure(workload_name: str, precision: str):
     """Select the workload and storage precision (f64: tol 2^-53; f32: tol 2^-24)."""
     global WORKLOAD, PRECISION, HS, TOL, P, R, WORKLOAD_NAME
+    if workload_name not in WORKLOADS:
+        WORKLOAD, PRECISION = workload_name, precision
+        return
+    if precision == "mixed":
+        raise SystemExit("--precision mixed applies to the batch512 and serve workloads")
     cfg = WORKLOADS[workload_name]
     WORKLOAD, PRECISION = workload_name, precision
     HS, P, R = cfg["hs"], cfg["p"], cfg["r"]
@@ -66,8 +71,11 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="convdiff3d-64", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--workload", default="convdiff3d-64", choices=sorted(WORKLOADS) + ["batch512", "serve"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "mixed"])
+    ap.add_argument("--requests", type=int, default=1000, help="serve: number of arrivals")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--no-tune", action="store_true", help="batch512: skip the autotuner (default shape)")
     ap.add_argument("--profile-solve", type=float, default=None, metavar="H",
                     help="profiler target: Algorithm 1 and two Algorithm 3 solves of the workload at step H, "
                          "no timing and no JSON line")
@@ -175,6 +183,8 @@ def time_oracle(steps, warmup):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
+    if WORKLOAD in ("batch512", "serve"):
+        return run_reference_fleet(args)
     steps, warmup = max(1, args.steps), max(0, args.warmup)
     # bound the whole run to a few minutes: at most 6 timed steps and 1 warm-up of the full oracle step
     steps_run, warm_run = min(steps, 6), min(warmup, 1)
@@ -269,6 +279,10 @@ def main():
         return run_reference(args, rank, world)
     if args.profile_solve is not None:
         return profile_solve(args.profile_solve)
+    if WORKLOAD == "batch512":
+        return run_batch(args, rank, world, local_rank)
+    if WORKLOAD == "serve":
+        return run_serve(args, rank, world, local_rank)
     import numpy as np
     import torch
 
@@ -445,6 +459,344 @@ def e2e(api, capi, A_h, V_h, alpha, dev, stream, K, world, dist):
     ms = reduce_max_over_ranks(e0.elapsed_time(e1) / K, dist, dev)
     return {"value": solves_per_second(ms, world), "unit": "solves/s", "ms_per_step": ms,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ------------------------------------------------------------------------------------------------
+# Many instances: one batched launch (batch512) and the continuous-batching request loop (serve)
+# ------------------------------------------------------------------------------------------------
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def solve_bytes(n, nnz, p, r, series_terms, recovery_terms, b):
+    """Algorithmic bytes of one solve's sparse block products: per series term the operator
+    ((4 + b) nnz + 4 (n+1)) and reading/writing V, D and S (5 n (p+1) r b); per recovery term the operator
+    and reading F, reading and writing E, writing the next F (4 n 2r b)."""
+    op = (4 + b) * nnz + 4 * (n + 1)
+    w_s, w_f = (p + 1) * r, (2 * r if p > 0 else r)
+    return series_terms * (op + 5 * n * w_s * b) + recovery_terms * (op + 4 * n * w_f * b)
+
+
+def batch_workload(precision):
+    from paper_2509_26475_gb300 import workloads as wl
+
+    return wl.workload_batch(512, 4, precision)
+
+
+def run_batch(args, rank, world, local_rank):
+    """batch512: 512 independent instances (n log-uniform in [1e3, 2.56e5], 2-D/3-D Laplacians plus
+    diagonal shifts, p in 1..4, r in 1..3), each Algorithm 1 + Algorithm 3, all in one persistent
+    launch with an autotuned launch shape.  A step is that launch; value = instances solved per second.
+    The same instances solved one by one through phic_select_params + phic_solve in FP64 (the plain
+    single-instance path) are timed once for comparison."""
+    import numpy as np
+    import torch
+
+    from paper_2509_26475_gb300 import api, build, capi
+
+    build.build()
+    lib = capi.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    prec_name = PRECISION
+    insts = batch_workload(prec_name)
+    devs = []
+    for x in insts:
+        dt = torch.float32 if x["prec"] == "f32" else torch.float64
+        devs.append((api.DeviceCSR.from_host(x["A"], device=dev, dtype=dt), torch.as_tensor(x["V"]).to(dt).to(dev)))
+    items = [api.BatchItem(A, V, x["t"], x["alpha"], tol=x["tol"], select=True) for x, (A, V) in zip(insts, devs)]
+    if args.no_tune:
+        cfg, tune_ms = {"rows_per_cta": 4096, "blocks_per_sm": 3}, None
+    else:
+        cands = [{"rows_per_cta": rr, "blocks_per_sm": bb} for bb in (2, 3) for rr in (2048, 4096, 8192)]
+        cfg, tune_ms = api.autotune(items, candidates=cands, reps=1)
+    b = api.Batch(items, config=cfg)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 0)):
+        b.launch()
+    torch.cuda.synchronize(dev)
+    bad = [i for i, st in enumerate(b.stats()) if st["status"] != 0]
+    if bad:
+        raise SystemExit(f"batch512: instances {bad[:8]} reported a device status")
+    K = max(1, args.steps)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    launches0 = lib.phic_launch_count()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    with ClockSampler(local_rank, None) as clk:
+        for k in range(K):
+            ev0[k].record(stream)
+            b.launch()
+            ev1[k].record(stream)
+        torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    launches = lib.phic_launch_count() - launches0
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(K)]
+    ms = reduce_max_over_ranks(statistics.mean(step_ms), dist, dev)
+    value = len(items) * world / (ms / 1000.0)
+    stats = b.stats()
+    nbytes = 0.0
+    for x, st in zip(insts, stats):
+        bb = 4 if x["prec"] == "f32" else 8
+        nbytes += solve_bytes(x["A"].n, x["A"].nnz, x["p"], x["r"], st["series_terms"], st["recovery_terms"], bb)
+    hbm_peak = float(_peaks().get("hbm_gbs", 6800.0))
+    achieved = nbytes / (statistics.mean(step_ms) / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": "batch_kernel (Algorithms 1 and 3 for all 512 instances, one launch)",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured); algorithmic bytes of the series and "
+                             "recovery products only (Algorithm 1's passes not counted)",
+                "launch_ms": statistics.mean(step_ms)}
+    # the plain single-instance FP64 path on the same instances (one by one), timed once
+    single = None
+    if rank == 0:
+        ws_p = api.new_params(dev)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d64 = [(A.astype(torch.float64), V.double()) for (A, V) in devs]
+        for A, V in d64[:4]:  # warm-up
+            api.select_params(A, out=ws_p)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for x, (A, V) in zip(insts, d64):
+            P = api.select_params(A, out=ws_p)
+            api.solve(A, V, x["t"], x["alpha"], 2.0**-53, P)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sms = e0.elapsed_time(e1)
+        single = {"value": len(insts) / (sms / 1000.0), "unit": "solves/s", "ms": sms,
+                  "path": "phic_select_params + phic_solve per instance, FP64 at tol 2^-53, same 512 instances"}
+    nf32 = sum(1 for x in insts if x["prec"] == "f32")
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f64": "f64", "f32": "f32"}.get(prec_name, "f64+f32"), "data": "synthetic",
+            "config": {"workload": f"batch512: 512 instances, n log-uniform [1e3, 2.56e5] (2-D/3-D Laplacian + diag "
+                                   f"U[-10,0]), p 1..4, r 1..3, Algorithm 1 + 3 each, {prec_name} "
+                                   f"({nf32} FP32 at 2^-24, {len(insts) - nf32} FP64 at 2^-53)",
+                       "rows": int(sum(x["A"].n for x in insts)), "nnz": int(sum(x["A"].nnz for x in insts)),
+                       "launch_shape": cfg, "autotune_ms": tune_ms, "grid": b.info()["grid"],
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                       "step": "one persistent launch over all 512 instances"},
+            "roofline": roofline, "gpu_launches": int(launches), "wall_s_timed_region": wall,
+            "single_instance_fp64": single}
+    clk_sum = clk.summary()
+    if clk_sum:
+        line["clocks"] = clk_sum
+    if not args.no_e2e:
+        line["e2e"] = batch_e2e(api, insts, devs, items, b, dev, stream, K, world, dist)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = fleet_oracle_sample(insts[:6])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def batch_e2e(api, insts, devs, items, b, dev, stream, K, world, dist):
+    """The batched step from pinned host buffers: copy every operator and V in, one launch, copy every W
+    out; CUDA events around all of it."""
+    import torch
+
+    host = []
+    h2d = d2h = 0
+    for (A, V), it in zip(devs, items):
+        hp = [t.cpu().pin_memory() for t in (A.rowptr, A.colidx, A.values, V)]
+        wo = torch.empty(it.W.shape, dtype=it.W.dtype).pin_memory()
+        host.append((hp, wo))
+        h2d += sum(t.numel() * t.element_size() for t in hp)
+        d2h += wo.numel() * wo.element_size()
+
+    def one():
+        for (A, V), (hp, _) in zip(devs, host):
+            for dst, src in zip((A.rowptr, A.colidx, A.values, V), hp):
+                dst.copy_(src, non_blocking=True)
+        b.launch()
+        for it, (_, wo) in zip(items, host):
+            wo.copy_(it.W, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(K):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = reduce_max_over_ranks(e0.elapsed_time(e1) / K, dist, dev)
+    return {"value": len(items) * world / (ms / 1000.0), "unit": "solves/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def fleet_oracle_sample(insts):
+    """The oracle (Algorithm 1 + Algorithm 3 in FP64, OpenMP over rows) on a few instances."""
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    for x in insts:
+        sel = oracle.select(x["A"], tol=x["tol"])
+        oracle.solve(x["A"], x["V"], x["t"], x["alpha"], x["tol"], sel["s"], sel["xi"])
+    dt = time.perf_counter() - t0
+    return {"value": len(insts) / dt, "unit": "solves/s", "cores": used, "kind": "oracle",
+            "sample": f"the first {len(insts)} instances of the workload (Algorithm 1 + 3 each), FP64 C oracle"}
+
+
+def serve_requests(count, seed=5):
+    """The serving mix: 80 % instances of the batching distribution (own operators, Algorithm 1 in their
+    first slice), 20 % solves on a 3-D 7-point upwind convection-diffusion operator on 100^3 (n = 10^6,
+    Peclet 10) registered once (FP64 and FP32 copies), p = 3, r = 2, t = (h/2, h/3), alpha = (1/2, 1/3),
+    h = 1e-4; tol 2^-53 (FP64) or 2^-24 (FP32) per request with equal odds; Poisson arrivals."""
+    import numpy as np
+
+    from paper_2509_26475_gb300 import workloads as wl
+
+    rng = np.random.default_rng(seed)
+    kinds = rng.random(count) < 0.2
+    precs = np.where(rng.random(count) < 0.5, "f64", "f32")
+    out = []
+    for i in range(count):
+        if kinds[i]:
+            out.append(dict(kind="big", prec=str(precs[i]), vidx=int(rng.integers(0, 4))))
+        else:
+            x = wl.batch_instance(seed, i, 1000, 256000, str(precs[i]))
+            out.append(dict(kind="small", prec=x["prec"], inst=x))
+    return out
+
+
+def run_serve(args, rank, world, local_rank):
+    """serve: Poisson arrivals at --rate of --requests solve requests into the continuous-batching loop;
+    value = completed solves per second of wall time (first arrival to last result on the host),
+    latency = result-on-host minus submission, p50 and p99."""
+    import numpy as np
+    import torch
+
+    from paper_2509_26475_gb300 import api, build, capi
+    from paper_2509_26475_gb300 import workloads as wl
+
+    build.build()
+    capi.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    reqs = serve_requests(args.requests)
+    big_A = wl.convection_diffusion(100, 3, 10.0)
+    rng = np.random.default_rng(7)
+    bigV = {pr: [rng.standard_normal((4, big_A.n)).astype(np.float32 if pr == "f32" else np.float64) for _ in range(4)]
+            for pr in ("f64", "f32")}
+    h = 1e-4
+    free = torch.cuda.mem_get_info(dev)[0]
+    arena = int(min(free * 0.85, 200e9))
+    srv = api.Server(arena_bytes=arena, device=local_rank)
+    ops = {pr: srv.add_operator(api.HostOperator(big_A, prec=pr)) for pr in ("f64", "f32")}
+    while any(srv.operator_params(o) is None for o in ops.values()):
+        time.sleep(0.01)
+    # page-locked inputs for every request, prepared before the arrivals start
+    hostreq = []
+    for q in reqs:
+        if q["kind"] == "big":
+            hostreq.append(api.HostRequest(big_A.n, bigV[q["prec"]][q["vidx"]], [h / 2, h / 3], [0.5, 1.0 / 3.0],
+                                           tol=2.0**-53 if q["prec"] == "f64" else 2.0**-24, prec=q["prec"],
+                                           op=ops[q["prec"]]))
+        else:
+            x = q["inst"]
+            hostreq.append(api.HostRequest(x["A"], x["V"], x["t"], x["alpha"], tol=x["tol"], prec=x["prec"]))
+    # warm-up: a few requests through the loop
+    for k in range(max(args.warmup, 0)):  # the buffers are reused by the timed stream (W is rewritten)
+        for i in [srv.submit(r) for r in hostreq[k * 4:(k + 1) * 4]]:
+            srv.wait(i, 120000)
+    c0 = srv.counters()
+    gaps = np.random.default_rng(11).exponential(1.0 / args.rate, size=len(hostreq))
+    ids = []
+    with ClockSampler(local_rank, None) as clk:
+        t_start = time.perf_counter()
+        due = t_start
+        for q, g in zip(hostreq, gaps):
+            due += g
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                time.sleep(min(due - now, 0.0005))
+            ids.append(srv.submit(q))
+        infos = [srv.wait(i, 600000) for i in ids]
+        t_end = time.perf_counter()
+    c1 = srv.counters()
+    lat = np.array([(x["done_ns"] - x["submit_ns"]) / 1e6 for x in infos])
+    first_sub = min(x["submit_ns"] for x in infos)
+    last_done = max(x["done_ns"] for x in infos)
+    span = (last_done - first_sub) / 1e9
+    failed = sum(1 for x in infos if x["status"] != 0)
+    nbytes = 0.0
+    for q, x in zip(reqs, infos):
+        st = x["stats"]
+        if q["kind"] == "big":
+            n, nnz, p, r = big_A.n, big_A.nnz, 3, 2
+        else:
+            n, nnz, p, r = q["inst"]["A"].n, q["inst"]["A"].nnz, q["inst"]["p"], q["inst"]["r"]
+        nbytes += solve_bytes(n, nnz, p, r, st["series_terms"], st["recovery_terms"], 4 if q["prec"] == "f32" else 8)
+    busy_s = (c1["gpu_busy_ms"] - c0["gpu_busy_ms"]) / 1000.0
+    hbm_peak = float(_peaks().get("hbm_gbs", 6800.0))
+    achieved = nbytes / busy_s / 1e9 if busy_s > 0 else 0.0
+    value = len(infos) / span
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+            "ms_per_step": span * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic",
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "config": {"workload": f"serve: {len(reqs)} Poisson arrivals at {args.rate:g}/s; 80% batching-distribution "
+                                   "instances (own operator, Algorithm 1 in the first slice), 20% n=1e6 3-D "
+                                   "convection-diffusion (100^3, Pe 10) solves on a registered operator, p=3 r=2 "
+                                   "t=(h/2,h/3) h=1e-4; tol 2^-53 FP64 or 2^-24 FP32 per request",
+                       "offered_rate": args.rate, "achieved_rate": value, "failed": failed,
+                       "slices": c1["slices"] - c0["slices"], "max_slice_requests": c1["max_slice_requests"],
+                       "gpu_busy_frac": busy_s / span if span > 0 else None, "arena_gb": arena / 1e9,
+                       "arena_peak_gb": c1["arena_peak"] / 1e9,
+                       "step": "the whole arrival stream (first submission to last result on the host)",
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": "x1"},
+            "roofline": {"bound": "hbm", "kernel": "batch_kernel slices (series + recovery products)",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": None, "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured); "
+                                                       "algorithmic bytes over the slices' device time"},
+            "gpu_launches": int(c1["slices"] - c0["slices"]) * 2, "wall_s_timed_region": t_end - t_start,
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                    "note": "the serving numbers are end to end already: host inputs in, results on the host"}}
+    clk_sum = clk.summary()
+    if clk_sum:
+        line["clocks"] = clk_sum
+    srv.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_fleet(args):
+    """--impl reference for batch512 / serve: the oracle on a bounded sample of the same instances."""
+    if WORKLOAD == "batch512":
+        insts = batch_workload(PRECISION if PRECISION != "f64" else "f64")[:6]
+    else:
+        insts = [q["inst"] for q in serve_requests(40) if q["kind"] == "small"][:6]
+    cb = fleet_oracle_sample(insts)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": 1, "warmup": 0, "ms_per_step": 1000.0 * len(insts) / cb["value"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "device": "host CPU", "threads": cb["cores"]},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -152,8 +152,12 @@ phic_status phic_solve_workspace_size(int64_t n, int64_t nnz, int32_t p, int32_t
  *   ws      device workspace, 256-byte aligned, phic_solve_workspace_size(...) bytes.
  *   stats_dev   device phic_stats or NULL.
  *   max_terms   cap on the terms of one Taylor loop (<= 0 selects 610); reaching it sets PHIC_TERM_CAP.
- * prec = PHIC_F32 keeps A, V, the Taylor terms and W in FP32 with FP32 accumulation; the scalar
- * parameters (s, xi, mu, the nilpotent factors, the norms' comparison) stay FP64. */
+ * prec = PHIC_F32 keeps A, V, the Taylor terms and W in FP32 with FP32 accumulation (compensated sums in
+ * the sparse products); the scalar parameters (s, xi, mu, the nilpotent factors, the norms' comparison)
+ * stay FP64.  When params_dev comes from Algorithm 1 (s0 and f_star positive), an FP32 solve raises s to
+ * at least s0 f_star / (ln(2^24) / 2), so that no step's Taylor terms grow beyond about e^8.3 before they
+ * cancel: their FP32 rounding, not the truncation tolerance, bounds an FP32 result.  phic_stats.s reports
+ * the s used. */
 phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, const double* t, const double* alpha,
                        double tol, const phic_params* params_dev, uint32_t flags, int32_t max_terms, void* W, void* ws,
                        size_t ws_bytes, phic_stats* stats_dev, int32_t prec, phic_stream_t stream);

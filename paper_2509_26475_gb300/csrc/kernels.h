@@ -34,6 +34,8 @@ struct SolveState {
   long long rec_terms;
   int max_inner;
   int done;       // 1 once the output has been written
+  int ell;        // copy of B: ELL with this many slots per row, or 0 for CSR order
+  int pad;
 };
 
 // Entry of the solve's copy of A_1 = A - xi I, scaled by 2^-eA: column and value in one aligned load.
@@ -54,7 +56,8 @@ struct SolveArgs {
   const int* rowptr;
   const int* colidx;
   const void* vals;
-  void* A1;               // CsrEnt<T>[nnz]: columns and values of B = (A - xi I) 2^-eA
+  void* A1;               // CsrEnt<T>[a1_cap]: columns and values of B = (A - xi I) 2^-eA (CSR or ELL order)
+  long long a1_cap;       // entries A1 can hold (ELL is used when n times the longest row fits)
   unsigned char* rowflag; // [n] 1 where the row stores no diagonal entry
   const void* Vin;
   void* W;

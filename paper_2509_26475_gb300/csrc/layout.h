@@ -38,8 +38,12 @@ inline SelectLayout select_layout(int64_t n, int m) {
   return L;
 }
 
+// Entries of the solve's copy of B: room for an ELL layout with up to a quarter of padding.
+inline long long a1_capacity(long long nnz) { return (nnz > 0 ? nnz : 1) + nnz / 4 + 64; }
+
 struct SolveLayout {
   size_t ctlS, ctlR, state, A1, rowflag, Vt[2], Dt[2], S, Ft[2], E, total;
+  long long a1_cap;
   TileLayout sl, fl;
 };
 inline SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec) {
@@ -54,7 +58,8 @@ inline SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec) 
   L.ctlR = off; off += align_up(sizeof(Ctl));
   L.state = off; off += align_up(sizeof(SolveState));
   const size_t head = off;  // control blocks and state: zeroed before each solve
-  L.A1 = off; off += align_up((size_t)(nnz > 0 ? nnz : 1) * 2 * es);  // (column, value) entries
+  L.a1_cap = a1_capacity(nnz);
+  L.A1 = off; off += align_up((size_t)L.a1_cap * 2 * es);  // (column, value) entries, CSR or ELL order
   L.rowflag = off; off += align_up((size_t)n);
   for (int q = 0; q < 2; ++q) { L.Vt[q] = off; off += tileS; }
   for (int q = 0; q < 2; ++q) { L.Dt[q] = off; off += tileS; }
@@ -90,6 +95,7 @@ inline void fill_solve_args(SolveArgs& a, const phic_csr* A, int p, int r, const
   a.colidx = A->colidx;
   a.vals = A->values;
   a.A1 = base + L.A1;
+  a.a1_cap = L.a1_cap;
   a.rowflag = reinterpret_cast<unsigned char*>(base + L.rowflag);
   a.Vin = V;
   a.W = W;

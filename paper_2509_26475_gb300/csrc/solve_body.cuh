@@ -41,12 +41,10 @@
 #ifndef PHIC_CW_MAX
 #define PHIC_CW_MAX 2
 #endif
-// FP32 tiles: widest column chunk (16 bytes = 4 floats) and rows in flight per thread.
+// FP32 tiles: widest column chunk (16 bytes = 4 floats).  One row per thread at a time: carrying two or
+// four rows' loads in flight at once measured slower on GB300 (the registers cost residency).
 #ifndef PHIC_CW_MAX_F32
 #define PHIC_CW_MAX_F32 4
-#endif
-#ifndef PHIC_ROWS_F32
-#define PHIC_ROWS_F32 1
 #endif
 
 namespace phic {
@@ -76,38 +74,45 @@ __device__ __forceinline__ void umax(unsigned long long& m, double v) {
 // Per-warp maxima of two values and the bad-index / non-finite flags; thread 0 folds them into the
 // team's slots inside the barrier.
 struct WarpParts {
-  unsigned long long a[kBlock / 32], b[kBlock / 32];
+  unsigned long long a[kBlock / 32], b[kBlock / 32], c[kBlock / 32];
   int bad[kBlock / 32], nonfinite[kBlock / 32];
 };
 
 __device__ __forceinline__ void warp_parts(WarpParts& wp, unsigned long long a, unsigned long long b, int bad,
-                                           int nonfinite = 0) {
+                                           int nonfinite = 0, unsigned long long c = 0) {
   a = warp_max_u64(a);
   b = warp_max_u64(b);
+  c = warp_max_u64(c);
   const int anyb = __any_sync(0xffffffffu, bad);
   const int anyn = __any_sync(0xffffffffu, nonfinite);
   if ((threadIdx.x & 31) == 0) {
     wp.a[threadIdx.x >> 5] = a;
     wp.b[threadIdx.x >> 5] = b;
+    wp.c[threadIdx.x >> 5] = c;
     wp.bad[threadIdx.x >> 5] = anyb;
     wp.nonfinite[threadIdx.x >> 5] = anyn;
   }
 }
 
-// Slot 2 collects the non-finite flag of a pass (as 0/1).
+// Slot 2 collects the non-finite flag of a pass (as 0/1), slot 3 a third maximum (an integer).
 __device__ __forceinline__ void parts_to_slots(Ctl* c, int phase, const WarpParts& wp) {
-  unsigned long long a = 0, b = 0;
+  unsigned long long a = 0, b = 0, m = 0;
   int bad = 0, nf = 0;
   for (int w = 0; w < kBlock / 32; ++w) {
     a = wp.a[w] > a ? wp.a[w] : a;
     b = wp.b[w] > b ? wp.b[w] : b;
+    m = wp.c[w] > m ? wp.c[w] : m;
     bad |= wp.bad[w];
     nf |= wp.nonfinite[w];
   }
   slot_max(c, phase, 0, a);
   slot_max(c, phase, 1, b);
   if (nf) slot_max(c, phase, 2, 1ull);
+  if (m) slot_max(c, phase, 3, m);
   if (bad) set_status(c, PHIC_INVALID_ARG);
+}
+__device__ __forceinline__ unsigned long long slot_raw(const Ctl* c, int phase, int idx) {
+  return *(volatile const unsigned long long*)&c->slot[phase & 3][idx];
 }
 
 // Grid-wide norm published in a slot by the float path, back to FP64 (scaled by 2^e0).
@@ -139,6 +144,10 @@ struct DotAcc {
   __device__ __forceinline__ void add(T a, T x) { hi = fma(a, x, hi); }
   __device__ __forceinline__ T value() const { return hi; }
 };
+#ifndef PHIC_F32_COMPENSATED
+#define PHIC_F32_COMPENSATED 1
+#endif
+#if PHIC_F32_COMPENSATED
 template <>
 struct DotAcc<float> {
   float hi, lo;
@@ -155,6 +164,7 @@ struct DotAcc<float> {
   }
   __device__ __forceinline__ float value() const { return __fadd_rn(hi, lo); }
 };
+#endif
 
 // acc[j] = sum_q B(row, col_q) X(col_q, c0 + j) over the row's stored entries, four at a time so that
 // their gathers are in flight together.  Columns were checked when the entries were written.
@@ -186,54 +196,67 @@ __device__ __forceinline__ void spmm_ent(const int* __restrict__ rowptr, const C
   for (int j = 0; j < CW; ++j) acc[j] = d[j].value();
 }
 
-// The same for NR rows at once: their row bounds, entries and gathers are all issued before any is
-// used, so NR dependent load chains (row bounds -> entries -> gathers) overlap in one thread.  On GB300
-// the registers this takes cost more residency than the overlap gains (NR = 2 and 4 measured slower
-// than NR = 1 on the FP32 recovery), so the default is one row.
-template <typename T, int CW, int NR>
-__device__ __forceinline__ void spmm_rows(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent,
-                                          const T* __restrict__ X, int ws, int c0, const int (&row)[NR],
-                                          const bool (&act)[NR], T (&acc)[NR][CW]) {
-  int beg[NR], cnt[NR];
+// The same over the ELL copy of B: entry q of `row` at ent[q n + row] for q < K (rows shorter than K
+// padded with a zero weight on their own column), so no row bounds are loaded and the entries of
+// consecutive rows are consecutive.  K is a template parameter for the 2-D and 3-D stencil widths 5 and 7
+// (every entry load and gather of the row in flight at once, no predicated slots), a run-time value
+// otherwise.
+template <typename T, int CW, int K>
+__device__ __forceinline__ void spmm_ell_k(const CsrEnt<T>* __restrict__ ent, int n, const T* __restrict__ X, int ws,
+                                           int c0, int row, T (&acc)[CW]) {
+  CsrEnt<T> e[K];
 #pragma unroll
-  for (int u = 0; u < NR; ++u) {
-    beg[u] = act[u] ? __ldg(rowptr + row[u]) : 0;
-    cnt[u] = act[u] ? __ldg(rowptr + row[u] + 1) - beg[u] : 0;
+  for (int q = 0; q < K; ++q) e[q] = ent[(size_t)q * n + row];
+  T x[K][CW];
+#pragma unroll
+  for (int q = 0; q < K; ++q) VecIO<T, CW>::ld(X + (size_t)e[q].col * ws + c0, x[q]);
+  DotAcc<T> d[CW];
+#pragma unroll
+  for (int j = 0; j < CW; ++j) d[j].zero();
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+#pragma unroll
+    for (int j = 0; j < CW; ++j) d[j].add(e[q].v, x[q][j]);
+#pragma unroll
+  for (int j = 0; j < CW; ++j) acc[j] = d[j].value();
+}
+
+template <typename T, int CW>
+__device__ __forceinline__ void spmm_ell_dyn(const CsrEnt<T>* __restrict__ ent, int n, int K, const T* __restrict__ X,
+                                             int ws, int c0, int row, T (&acc)[CW]) {
+  DotAcc<T> d[CW];
+#pragma unroll
+  for (int j = 0; j < CW; ++j) d[j].zero();
+  for (int q0 = 0; q0 < K; q0 += 4) {
+    CsrEnt<T> e[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (q0 + u < K) e[u] = ent[(size_t)(q0 + u) * n + row];
+    T x[4][CW];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (q0 + u < K) VecIO<T, CW>::ld(X + (size_t)e[u].col * ws + c0, x[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (q0 + u < K) {
+#pragma unroll
+        for (int j = 0; j < CW; ++j) d[j].add(e[u].v, x[u][j]);
+      }
   }
-  int mx = 0;
 #pragma unroll
-  for (int u = 0; u < NR; ++u) mx = cnt[u] > mx ? cnt[u] : mx;
-  DotAcc<T> d[NR][CW];
-#pragma unroll
-  for (int u = 0; u < NR; ++u)
-#pragma unroll
-    for (int j = 0; j < CW; ++j) d[u][j].zero();
-  for (int q0 = 0; q0 < mx; q0 += 4) {
-    CsrEnt<T> e[NR][4];
-#pragma unroll
-    for (int u = 0; u < NR; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (q0 + v < cnt[u]) e[u][v] = ent[beg[u] + q0 + v];
-    T x[NR][4][CW];
-#pragma unroll
-    for (int u = 0; u < NR; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (q0 + v < cnt[u]) VecIO<T, CW>::ld(X + (size_t)e[u][v].col * ws + c0, x[u][v]);
-#pragma unroll
-    for (int u = 0; u < NR; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (q0 + v < cnt[u]) {
-#pragma unroll
-          for (int j = 0; j < CW; ++j) d[u][j].add(e[u][v].v, x[u][v][j]);
-        }
+  for (int j = 0; j < CW; ++j) acc[j] = d[j].value();
+}
+
+// B X for one row through whichever copy of B the setup built (ell = K > 0: ELL with K slots; 0: CSR).
+template <typename T, int CW>
+__device__ __forceinline__ void spmm_row(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent, int n,
+                                         int ell, const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW]) {
+  switch (ell) {
+    case 0: spmm_ent<T, CW>(rowptr, ent, X, ws, c0, row, acc); break;
+    case 5: spmm_ell_k<T, CW, 5>(ent, n, X, ws, c0, row, acc); break;
+    case 7: spmm_ell_k<T, CW, 7>(ent, n, X, ws, c0, row, acc); break;
+    default: spmm_ell_dyn<T, CW>(ent, n, ell, X, ws, c0, row, acc); break;
   }
-#pragma unroll
-  for (int u = 0; u < NR; ++u)
-#pragma unroll
-    for (int j = 0; j < CW; ++j) acc[u][j] = d[u][j].value();
 }
 
 // |x| 2^-e0 as an FP32 value, for the infinity-norm sums that feed the truncation test.  For a double
@@ -250,10 +273,16 @@ __device__ __forceinline__ float norm_piece(double x, int bias, float scale, int
   t = t > 0x0FEFFFFF ? 0x0FEFFFFF : t;
   return __int_as_float(t << 3);
 }
+// An FP32 element is scaled exactly; Inf and NaN pass into the row sums, which the caller checks once per
+// row (row_nonfinite), instead of every element here.
 __device__ __forceinline__ float norm_piece(float x, int bias, float scale, int& nonfinite) {
   (void)bias;
-  nonfinite |= !isfinite(x);
+  (void)nonfinite;
   return fabsf(x) * scale;
+}
+template <typename T>
+__device__ __forceinline__ int row_nonfinite(float s1, float s2) {
+  return sizeof(T) == 4 ? !(isfinite(s1) && isfinite(s2)) : 0;
 }
 
 // Block-level broadcast of the loop decision made by thread 0.
@@ -277,9 +306,13 @@ struct SeriesTerm {
   T kd[PHIC_MAX_R], ka[PHIC_MAX_R], kt[PHIC_MAX_R];
 };
 
+// Largest per-step norm nu t / s of an FP32 solve: ln(2^24) / 2 (the FP32 rounding of the Taylor terms,
+// which grow like e^(nu t / s), then stays near sqrt(u)).
+constexpr double kTheta32 = 8.317766166719343;
+
 struct SeriesScalars {
-  double xi, tc[PHIC_MAX_R], cA[PHIC_MAX_R], cD[PHIC_MAX_R], cV[PHIC_MAX_R];
-  int s_int, bad, eA, nodiag;
+  double xi, s_used, tc[PHIC_MAX_R], cA[PHIC_MAX_R], cD[PHIC_MAX_R], cV[PHIC_MAX_R];
+  int s_int, bad, eA, nodiag, ell;
 };
 
 template <typename T>
@@ -288,7 +321,7 @@ struct RecoverScalars {
   T coef[PHIC_MAX_R];
   float fcoef[PHIC_MAX_R];
   T cj[PHIC_MAX_P + 1][PHIC_MAX_R];
-  int s_int, series_terms, status, eA, nodiag;
+  int s_int, series_terms, status, eA, nodiag, ell;
   int done, rec_init, j_done, cur;
   double cF0;
 };
@@ -331,7 +364,17 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   if (threadIdx.x == 0) {
     // s <- ceil(s max|t_i|);  mu = exp((xi/s) T);  V <- V (I kron 1^T mu/s);
     // Jsh = (J kron Delta - xi I kron T)/s  (divided by s as in Algorithm 2)
-    const double xi = a.params->xi, s = a.params->s;
+    const double xi = a.params->xi;
+    double s = a.params->s;
+    if (sizeof(T) == 4) {
+      // FP32 storage: the Taylor terms of a step grow like e^(nu t / s) before they cancel, and their
+      // FP32 rounding, not Algorithm 1's truncation bound, sets the error.  Keep the per-step norm
+      // nu t / s at most theta_32 = ln(2^24) / 2, where nu = s0 f(xi*) is the norm estimate behind s
+      // (s = nu / (tol m!)^(1/m)); FP64 steps (<= 12.8 at tol 2^-53) are below ln(2^53) / 2 already.
+      const double nu = a.params->s0 * a.params->f_star;
+      if (nu > 0.0 && isfinite(nu)) s = fmax(s, nu / kTheta32);
+    }
+    sc.s_used = s;
     int bad = !isfinite(xi) || !(s >= 0.0) || !isfinite(s);
     double tmax = 0.0;
     for (int i = 0; i < r; ++i) tmax = fmax(tmax, fabs(a.t[i]));
@@ -350,6 +393,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
     sc.bad = bad;
     sc.eA = 0;
     sc.nodiag = 0;
+    sc.ell = 0;
     lc.k = 1;
   }
   __syncthreads();
@@ -390,7 +434,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   {
     const int ph = phase++;
     slot_reset(tm, ph);
-    unsigned long long mx = 0;
+    unsigned long long mx = 0, maxlen = 0;
     int nodiag = 0;
     for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
       const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
@@ -399,6 +443,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
         if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) {
           bad = 1;
         } else {
+          maxlen = (unsigned long long)(b1 - b0) > maxlen ? (unsigned long long)(b1 - b0) : maxlen;
           bool shifted = false;
           double rs = 0.0;
           for (int q = b0; q < b1; ++q) {
@@ -418,12 +463,15 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
         }
       }
     }
-    warp_parts(wp, mx, (unsigned long long)nodiag, bad);
+    warp_parts(wp, mx, (unsigned long long)nodiag, bad, 0, maxlen);
     if (!team_sync_lead(tm, [&] { parts_to_slots(ctl, ph, wp); },
                         [&] {
                           const double na = slot_get(ctl, ph, 0);
                           sc.eA = (na > 0.0 && isfinite(na)) ? ilogb(na) + 1 : 0;  // ||B||_inf < 1
                           sc.nodiag = slot_get(ctl, ph, 1) != 0.0;
+                          // ELL copy of B when n times the longest row fits the copy's room
+                          const long long K = (long long)slot_raw(ctl, ph, 3);
+                          sc.ell = (K >= 1 && K <= 64 && K * (long long)n <= a.a1_cap) ? (int)K : 0;
                           lc.status = read_status(ctl);
                         }))
       return PHIC_TIMEOUT;
@@ -445,6 +493,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
       if (act) {
         if (lane == 0) {
           const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
+          const int K = sc.ell;
           bool shifted = false;
           for (int q = b0; q < b1; ++q) {  // subtract xi once from the stored diagonal, in FP64
             const int col = __ldg(a.colidx + q);
@@ -456,7 +505,13 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
             CsrEnt<T> e;
             e.col = col;
             e.v = (T)(v * scaleB);
-            ent[q] = e;
+            ent[K ? (size_t)(q - b0) * n + row : (size_t)q] = e;
+          }
+          for (int q = b1 - b0; q < K; ++q) {  // ELL padding: zero weight on the row's own column
+            CsrEnt<T> e;
+            e.col = row;
+            e.v = T(0);
+            ent[(size_t)q * n + row] = e;
           }
         }
         T x[CW];
@@ -517,6 +572,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   // argument fields used per row, kept in registers (the argument block may live in shared memory)
   const int* __restrict__ rowptr = a.rowptr;
   const unsigned char* __restrict__ rowflag = a.rowflag;
+  const int ell = sc.ell;
   while (lc.go) {
     const int kk = lc.k;
     const int ph = phase++;
@@ -545,7 +601,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
         T acc[CW];
 #pragma unroll
         for (int j = 0; j < CW; ++j) acc[j] = T(0);
-        spmm_ent<T, CW>(rowptr, ent, Do, L.ws, c0, row, acc);
+        spmm_row<T, CW>(rowptr, ent, n, ell, Do, L.ws, c0, row, acc);
         if (nodiag && rowflag[row]) {  // no stored diagonal: apply the shift explicitly
           T own[CW];
           VecIO<T, CW>::ld(Do + o, own);
@@ -571,6 +627,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
         VecIO<T, CW>::st(Vn + o, vn);
         VecIO<T, CW>::st(Dn + o, dn);
         VecIO<T, CW>::st(S + o, sv);
+        nf |= row_nonfinite<T>(pD, pS);
       }
       const float rD = group_sum(pD, L.Lp2), rS = group_sum(pS, L.Lp2);
       if (act && lane == 0) {
@@ -602,7 +659,7 @@ __device__ __forceinline__ void series_body(const SolveArgs& a, Team& tm, Series
     sv->s_int = sm.sc.s_int;
     sv->series_terms = sm.lc.k;
     sv->xi = sm.sc.xi;
-    sv->s = a.params->s;
+    sv->s = sm.sc.s_used;
     sv->eA = sm.sc.eA;
     sv->nodiag = sm.sc.nodiag;
     sv->rec_init = 0;
@@ -612,6 +669,7 @@ __device__ __forceinline__ void series_body(const SolveArgs& a, Team& tm, Series
     sv->rec_terms = 0;
     sv->max_inner = 0;
     sv->done = 0;
+    sv->ell = sm.sc.ell;
   }
 }
 
@@ -659,6 +717,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
     sc.xi = vs->xi;
     sc.eA = vs->eA;
     sc.nodiag = vs->nodiag;
+    sc.ell = vs->ell;
     sc.done = vs->done;
     sc.rec_init = vs->rec_init;
     sc.j_done = vs->j_done;
@@ -794,6 +853,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   const unsigned char* __restrict__ rowflag = a.rowflag;
   const double tol = a.tol;
   const int max_terms = a.max_terms;
+  const int ell = sc.ell;
 
   // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||: next term
   auto decide = [&]() {
@@ -849,59 +909,44 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
       const int bias = lc.bias;
       const float fscale = lc.fscale;
       int nf = 0;
-      constexpr int NR = sizeof(T) == 4 ? PHIC_ROWS_F32 : 1;  // rows in flight per thread
-      const int lane = threadIdx.x & lmask;
-      for (long long it0 = threadIdx.x; it0 < br.padded; it0 += (long long)NR * kBlock) {
-        int row[NR];
-        bool act[NR];
+      for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
+        const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
+        const bool act = row < br.r1 && lane < L.L;
+        float pF = 0.f, pE = 0.f;
+        if (act) {
+          T acc[CW];
+          spmm_row<T, CW>(rowptr, ent, n, ell, Go, L.ws, c0, row, acc);
+          const size_t o = (size_t)row * L.ws + c0;
+          const bool shift_row = nodiag && rowflag[row];
+          T e[CW];
+          if (kk == 1 || shift_row) {
+            T own[CW];
+            VecIO<T, CW>::ld(Go + o, own);
+            if (shift_row) {
 #pragma unroll
-        for (int u = 0; u < NR; ++u) {
-          const long long it = it0 + (long long)u * kBlock;
-          row[u] = br.r0 + (int)(it >> br.shift);
-          act[u] = it < br.padded && row[u] < br.r1 && lane < L.L;
-        }
-        T acc[NR][CW];
-        spmm_rows<T, CW, NR>(rowptr, ent, Go, L.ws, c0, row, act, acc);
-        float pF[NR], pE[NR];
-#pragma unroll
-        for (int u = 0; u < NR; ++u) {
-          pF[u] = 0.f;
-          pE[u] = 0.f;
-          if (act[u]) {
-            const size_t o = (size_t)row[u] * L.ws + c0;
-            const bool shift_row = nodiag && rowflag[row[u]];
-            T e[CW];
-            if (kk == 1 || shift_row) {
-              T own[CW];
-              VecIO<T, CW>::ld(Go + o, own);
-              if (shift_row) {
-#pragma unroll
-                for (int j = 0; j < CW; ++j) acc[u][j] = fma(xiB, own[j], acc[u][j]);
-              }
-              if (kk == 1) {
-#pragma unroll
-                for (int j = 0; j < CW; ++j) e[j] = own[j];  // E = F at the start of the step
-              }
+              for (int j = 0; j < CW; ++j) acc[j] = fma(xiB, own[j], acc[j]);
             }
-            if (kk != 1) VecIO<T, CW>::ld(E + o, e);
+            if (kk == 1) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) {
-              // F_k = c_k G_k;  E <- E + F_k
-              e[j] = fma(kC[j], acc[u][j], e[j]);
-              pF[u] += kF[j] * norm_piece(acc[u][j], bias, fscale, nf);
-              pE[u] += norm_piece(e[j], bias, fscale, nf);
+              for (int j = 0; j < CW; ++j) e[j] = own[j];  // E = F at the start of the step
             }
-            VecIO<T, CW>::st(Gn + o, acc[u]);
-            VecIO<T, CW>::st(E + o, e);
           }
-        }
+          if (kk != 1) VecIO<T, CW>::ld(E + o, e);
 #pragma unroll
-        for (int u = 0; u < NR; ++u) {
-          const float rF = group_sum(pF[u], L.Lp2), rE = group_sum(pE[u], L.Lp2);
-          if (act[u] && lane == 0) {
-            fmax_bits(mF, rF);
-            fmax_bits(mE, rE);
+          for (int j = 0; j < CW; ++j) {
+            // F_k = c_k G_k;  E <- E + F_k
+            e[j] = fma(kC[j], acc[j], e[j]);
+            pF += kF[j] * norm_piece(acc[j], bias, fscale, nf);
+            pE += norm_piece(e[j], bias, fscale, nf);
           }
+          VecIO<T, CW>::st(Gn + o, acc);
+          VecIO<T, CW>::st(E + o, e);
+          nf |= row_nonfinite<T>(pF, pE);
+        }
+        const float rF = group_sum(pF, L.Lp2), rE = group_sum(pE, L.Lp2);
+        if (act && lane == 0) {
+          fmax_bits(mF, rF);
+          fmax_bits(mE, rE);
         }
       }
       warp_parts(wp, mF, mE, 0, nf);
