@@ -735,6 +735,11 @@ def run_serve(args, rank, world, local_rank):
         infos = [srv.wait(i, 600000) for i in ids]
         t_end = time.perf_counter()
     c1 = srv.counters()
+    bad = [i for i, x in enumerate(infos) if x["status"] != 0]
+    if bad:
+        srv.close()
+        raise SystemExit(f"serve: {len(bad)} of {len(infos)} requests reported a device status (first: request "
+                         f"{bad[0]}, status {infos[bad[0]]['status']}); no number is reported")
     lat = np.array([(x["done_ns"] - x["submit_ns"]) / 1e6 for x in infos])
     first_sub = min(x["submit_ns"] for x in infos)
     last_done = max(x["done_ns"] for x in infos)

@@ -186,6 +186,40 @@ phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t r, const vo
                                const double* alpha, double tol, const phic_params* params_dev, uint32_t flags,
                                int32_t max_terms, void* W, phic_stats* stats_dev, int32_t prec, phic_stream_t stream);
 
+/* ---- Matrix-free low-rank operators ----------------------------------------------------------------
+ * A = U W^T with U and W n x k (k <= PHIC_MAX_RANK), applied as x -> U (W^T x) with O(n k) work and no
+ * n x n matrix: the family of large test operators of the paper's third experiment (Section 6), where
+ * sum_j phi_j(tA) v_j has the closed form sum_j v_j / j! + U (t sum_j phi_{j+1}(tM) (W^T v_j)) for
+ * W = U M^T.  Algorithms 1 and 3 run as for CSR operators; each product with A takes one team-wide
+ * reduction Z = W^T X (k x width, summed in FP64) before its row pass, and A - xi I is applied with the
+ * shift on every row.  The bound on ||A - xi I||_inf that scales the Taylor terms is
+ * max_i sum_q |U_iq| sum_j |W_jq| + |xi|. */
+#define PHIC_MAX_RANK 8
+
+typedef struct {
+  int64_t n;
+  int32_t k;        /* rank, 1 <= k <= PHIC_MAX_RANK */
+  int32_t prec;     /* PHIC_F64 or PHIC_F32: the type of U and W */
+  const void* U;    /* device, n x k row-major: U(i, q) at U[i k + q] */
+  const void* W;    /* device, n x k row-major */
+} phic_lowrank;
+
+/* Workspace of phic_lowrank_select_params: that of phic_select_params plus the partial sums of W^T x. */
+phic_status phic_lowrank_select_workspace_size(int64_t n, int32_t k, int32_t m, size_t* bytes);
+
+/* Algorithm 1 for A = U W^T (FP64 arithmetic whatever A->prec); as phic_select_params otherwise. */
+phic_status phic_lowrank_select_params(const phic_lowrank* A, const phic_select_opts* opts, const double* v, void* ws,
+                                       size_t ws_bytes, phic_params* params_dev, phic_stream_t stream);
+
+/* Workspace of phic_lowrank_solve; requires (p+1) r k <= 256. */
+phic_status phic_lowrank_solve_workspace_size(int64_t n, int32_t k, int32_t p, int32_t r, int32_t prec, size_t* bytes);
+
+/* Algorithm 3 for A = U W^T; arguments as phic_solve (A->prec must equal prec; (p+1) r k <= 256). */
+phic_status phic_lowrank_solve(const phic_lowrank* A, int32_t p, int32_t r, const void* V, const double* t,
+                               const double* alpha, double tol, const phic_params* params_dev, uint32_t flags,
+                               int32_t max_terms, void* W, void* ws, size_t ws_bytes, phic_stats* stats_dev,
+                               int32_t prec, phic_stream_t stream);
+
 /* ---- Batched solves -------------------------------------------------------------------------------
  * Many independent instances (each its own A, p, r, t, alpha, tol and precision) in ONE persistent
  * cooperative launch.  The paper solves one instance per call; this interface serves workloads of many
@@ -313,10 +347,14 @@ typedef struct {
   size_t arena_bytes;
   int32_t rows_per_cta;      /* team sizing of the slices (<= 0 selects 4096) */
   int32_t blocks_per_sm;     /* 2 or 3 (<= 0 selects 2) */
-  int32_t max_steps;         /* recovery outer steps per request per slice (<= 0 selects 8) */
+  int32_t max_steps;         /* recovery outer steps per request per slice (<= 0 selects 4) */
   int32_t max_active;        /* requests per slice (<= 0 selects 1024) */
   int32_t device;            /* CUDA device of the worker thread */
   int32_t m;                 /* Algorithm 1's degree (<= 0 selects 61); delta 0.8, seed 0x5EED, 200 evaluations */
+  double slice_us;           /* time budget of a slice by the planner's cost model: requests already running
+                                always join; new ones join in arrival order while the budget lasts (at least
+                                one per slice).  The budget is scaled by the backlog (waiting requests / 16,
+                                between 1 and 16).  <= 0 selects 20000 us */
 } phic_server_config;
 
 /* An operator registered with the server: uploaded once, Algorithm 1 run once, then shared by every

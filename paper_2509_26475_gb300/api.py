@@ -139,7 +139,14 @@ def select_params(A: DeviceCSR, m: int = 61, tol: float = 2.0**-53, delta: float
     opts = capi.phic_select_opts()
     lib.phic_select_opts_default(ctypes.byref(opts))
     opts.m, opts.tol, opts.delta, opts.seed, opts.max_evals = int(m), float(tol), float(delta), int(seed) & (2**64 - 1), int(max_evals)
-    nbytes = select_workspace_bytes(A.n, m)
+    lowrank = isinstance(A, DeviceLowRank)
+    if lowrank:
+        out_sz = ctypes.c_size_t(0)
+        capi.check(lib.phic_lowrank_select_workspace_size(A.n, A.k, int(m), ctypes.byref(out_sz)),
+                   "phic_lowrank_select_workspace_size")
+        nbytes = int(out_sz.value)
+    else:
+        nbytes = select_workspace_bytes(A.n, m)
     ws = workspace if workspace is not None else workspaces.get("select", nbytes, dev)
     vptr = None
     if v is not None:
@@ -147,8 +154,9 @@ def select_params(A: DeviceCSR, m: int = 61, tol: float = 2.0**-53, delta: float
             raise ValueError("v must be a contiguous CUDA float64 tensor with n entries")
         vptr = v.data_ptr()
     c = A.struct()
-    st = lib.phic_select_params(ctypes.byref(c), ctypes.byref(opts), vptr, ws.data_ptr(), ws.numel(),
-                                params.data_ptr(), _stream_handle(stream))
+    fn = lib.phic_lowrank_select_params if lowrank else lib.phic_select_params
+    st = fn(ctypes.byref(c), ctypes.byref(opts), vptr, ws.data_ptr(), ws.numel(), params.data_ptr(),
+            _stream_handle(stream))
     capi.check(st, "phic_select_params")
     if check:
         (stream or torch.cuda.current_stream()).synchronize()
@@ -186,12 +194,20 @@ def solve(A: DeviceCSR, V: torch.Tensor, t, alpha, tol: float, params: torch.Ten
     if W.shape != (r, A.n) or W.dtype != dt or not W.is_contiguous():
         raise ValueError("out has the wrong shape or dtype")
     stats = stats if stats is not None else new_stats(dev)
-    nbytes = solve_workspace_bytes(A.n, A.nnz, p, r, prec)
+    lowrank = isinstance(A, DeviceLowRank)
+    if lowrank:
+        out_sz = ctypes.c_size_t(0)
+        capi.check(lib.phic_lowrank_solve_workspace_size(A.n, A.k, int(p), int(r), int(prec), ctypes.byref(out_sz)),
+                   "phic_lowrank_solve_workspace_size")
+        nbytes = int(out_sz.value)
+    else:
+        nbytes = solve_workspace_bytes(A.n, A.nnz, p, r, prec)
     ws = workspace if workspace is not None else workspaces.get(("solve", prec), nbytes, dev)
     c = A.struct()
-    st = lib.phic_solve(ctypes.byref(c), int(p), int(r), V.data_ptr(), t.ctypes.data, alpha.ctypes.data, float(tol),
-                        params.data_ptr(), int(flags), int(max_terms), W.data_ptr(), ws.data_ptr(), ws.numel(),
-                        stats.data_ptr(), int(prec), _stream_handle(stream))
+    fn = lib.phic_lowrank_solve if lowrank else lib.phic_solve
+    st = fn(ctypes.byref(c), int(p), int(r), V.data_ptr(), t.ctypes.data, alpha.ctypes.data, float(tol),
+            params.data_ptr(), int(flags), int(max_terms), W.data_ptr(), ws.data_ptr(), ws.numel(),
+            stats.data_ptr(), int(prec), _stream_handle(stream))
     capi.check(st, "phic_solve")
     if check:
         (stream or torch.cuda.current_stream()).synchronize()
@@ -493,11 +509,11 @@ class Server:
     """
 
     def __init__(self, arena_bytes: int = 4 << 30, rows_per_cta: int = 0, blocks_per_sm: int = 0,
-                 max_steps: int = 0, max_active: int = 0, device: int = 0, m: int = 0):
+                 max_steps: int = 0, max_active: int = 0, device: int = 0, m: int = 0, slice_us: float = 0.0):
         self.lib = capi.load()
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=f"cuda:{device}")
         cfg = capi.phic_server_config(self.arena.data_ptr(), self.arena.numel(), int(rows_per_cta), int(blocks_per_sm),
-                                      int(max_steps), int(max_active), int(device), int(m))
+                                      int(max_steps), int(max_active), int(device), int(m), float(slice_us))
         h = ctypes.c_void_p(0)
         capi.check(self.lib.phic_server_create(ctypes.byref(cfg), ctypes.byref(h)), "phic_server_create")
         self.handle = h
@@ -558,3 +574,41 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---- matrix-free low-rank operators -----------------------------------------------------------------
+@dataclass
+class DeviceLowRank:
+    """A = U W^T with U, W (n, k) contiguous CUDA tensors of one precision (k <= PHIC_MAX_RANK),
+    applied matrix-free; accepted by select_params and solve in place of a DeviceCSR."""
+
+    U: torch.Tensor
+    W: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.U.shape[0])
+
+    @property
+    def k(self) -> int:
+        return int(self.U.shape[1])
+
+    @property
+    def prec(self) -> int:
+        return prec_of(self.U.dtype)
+
+    @property
+    def nnz(self) -> int:
+        return 0
+
+    def struct(self) -> capi.phic_lowrank:
+        for x in (self.U, self.W):
+            if not x.is_cuda or not x.is_contiguous() or x.dim() != 2:
+                raise ValueError("U and W must be contiguous (n, k) CUDA tensors")
+        if self.U.shape != self.W.shape or self.U.dtype != self.W.dtype:
+            raise ValueError("U and W must have the same shape and dtype")
+        return capi.phic_lowrank(self.n, self.k, self.prec, self.U.data_ptr(), self.W.data_ptr())
+
+    @property
+    def rowptr(self):  # device of the operator, for the helpers that allocate next to it
+        return self.U

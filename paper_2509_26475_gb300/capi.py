@@ -18,6 +18,7 @@ PHIC_PHASE_SERIES, PHIC_PHASE_RECOVER = 0x10, 0x20
 PHIC_BATCH_SELECT, PHIC_BATCH_NO_SOLVE = 0x100, 0x200
 PHIC_MAX_R, PHIC_MAX_P, PHIC_MAX_WIDTH = 16, 15, 128
 PHIC_NOALLOC_MAX_BYTES = 32 << 20
+PHIC_MAX_RANK = 8
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "TERM_CAP", 4: "TIMEOUT", 5: "CUDA_ERROR",
                 6: "WORKSPACE_TOO_SMALL"}
@@ -51,6 +52,11 @@ class phic_stats(ctypes.Structure):
                 ("spmm_count", ctypes.c_int64), ("xi", ctypes.c_double), ("s", ctypes.c_double)]
 
 
+class phic_lowrank(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("prec", ctypes.c_int32), ("U", ctypes.c_void_p),
+                ("W", ctypes.c_void_p)]
+
+
 class phic_batch_item(ctypes.Structure):
     _fields_ = [("A", phic_csr), ("p", ctypes.c_int32), ("r", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("max_terms", ctypes.c_int32), ("V", ctypes.c_void_p), ("W", ctypes.c_void_p),
@@ -73,7 +79,7 @@ class phic_batch_info(ctypes.Structure):
 class phic_server_config(ctypes.Structure):
     _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t), ("rows_per_cta", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("max_steps", ctypes.c_int32), ("max_active", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("m", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("m", ctypes.c_int32), ("slice_us", ctypes.c_double)]
 
 
 class phic_request(ctypes.Structure):
@@ -124,6 +130,15 @@ SIGNATURES = [
     ("phic_solve_noalloc", ctypes.c_int, [ctypes.POINTER(phic_csr), ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
                                           ctypes.c_double, _P, ctypes.c_uint32, ctypes.c_int32, _P, _P,
                                           ctypes.c_int32, _P]),
+    ("phic_lowrank_select_workspace_size", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                          ctypes.POINTER(ctypes.c_size_t)]),
+    ("phic_lowrank_select_params", ctypes.c_int, [ctypes.POINTER(phic_lowrank), ctypes.POINTER(phic_select_opts), _P,
+                                                  _P, ctypes.c_size_t, _P, _P]),
+    ("phic_lowrank_solve_workspace_size", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                         ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    ("phic_lowrank_solve", ctypes.c_int, [ctypes.POINTER(phic_lowrank), ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
+                                          ctypes.c_double, _P, ctypes.c_uint32, ctypes.c_int32, _P, _P,
+                                          ctypes.c_size_t, _P, ctypes.c_int32, _P]),
     ("phic_batch_workspace_size", ctypes.c_int, [ctypes.POINTER(phic_batch_item), ctypes.c_int32,
                                                  ctypes.POINTER(phic_select_opts), ctypes.POINTER(ctypes.c_size_t)]),
     ("phic_batch_create", ctypes.c_int, [ctypes.POINTER(phic_batch_item), ctypes.c_int32,

@@ -79,6 +79,11 @@ struct SolveArgs {
   phic_stats* stats;
   unsigned long long spin_ns;
   int fault;
+  // low-rank operator A = U W^T (lr_k > 0; the CSR fields are unused then)
+  int lr_k;
+  const void* lrU;
+  const void* lrW;
+  double* lr_part;  // [team size][k w] partial sums of W^T X
 };
 
 // Rows per chunk of Algorithm 1's sums of squares (each chunk's partial is one 16-byte record).
@@ -103,6 +108,10 @@ struct SelectArgs {
   Ctl* ctl;
   phic_params* out;
   unsigned long long spin_ns;
+  int lr_k;           // low-rank operator A = U W^T (the CSR fields are unused then)
+  const void* lrU;
+  const void* lrW;
+  double* lr_part;
 };
 
 // One instance of a batched launch: its solve and selection arguments (both pointing at the instance's
@@ -137,6 +146,10 @@ cudaError_t launch_series(const SolveArgs& a, int prec, cudaStream_t st, int* gr
 cudaError_t launch_recover(const SolveArgs& a, int prec, cudaStream_t st, int* grid_out);
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t st, int* grid_out);
 cudaError_t launch_params_set(phic_params* p, double xi, double s, cudaStream_t st);
+// Low-rank operators: the same kernels' bodies with A applied as U (W^T x).
+cudaError_t launch_lr_series(const SolveArgs& a, int prec, cudaStream_t st);
+cudaError_t launch_lr_recover(const SolveArgs& a, int prec, cudaStream_t st);
+cudaError_t launch_lr_select(const SelectArgs& a, cudaStream_t st);
 int max_select_grid();
 void count_launch();
 int blocks_per_sm(int elem_bytes);

@@ -10,6 +10,13 @@ __global__ void __launch_bounds__(kBlock) select_kernel(const SelectArgs a) {
   select_body<VT>(a, tm, sh);
 }
 
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) lr_select_kernel(const SelectArgs a) {
+  __shared__ SelShared sh;
+  Team tm = grid_team(a.ctl, a.spin_ns);
+  select_body<VT, true>(a, tm, sh);
+}
+
 __global__ void params_set_kernel(phic_params* p, double xi, double s) {
   p->xi = xi;
   p->s = s;
@@ -41,6 +48,28 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t st, int* grid_out) {
   if (need < grid) grid = need < 1 ? 1 : need;
   if (grid > max_select_grid()) grid = max_select_grid();
   if (grid_out) *grid_out = (int)grid;
+  void* args[] = {const_cast<SelectArgs*>(&a)};
+  count_launch();
+  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, st);
+}
+
+cudaError_t launch_lr_select(const SelectArgs& a, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const void* fn = a.vals_f32 ? (const void*)lr_select_kernel<float> : (const void*)lr_select_kernel<double>;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  if (per_sm > 2) per_sm = 2;
+  long long need = ((long long)a.n + kSelectChunk - 1) / kSelectChunk;
+  long long grid = (long long)sms * per_sm;
+  if (need < grid) grid = need < 1 ? 1 : need;
+  if (grid > kLowRankMaxGrid) grid = kLowRankMaxGrid;
   void* args[] = {const_cast<SelectArgs*>(&a)};
   count_launch();
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, st);

@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "lowrank.cuh"
 
 namespace phic {
 
@@ -114,6 +115,7 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
 }
 
 struct SelShared {
+  double lz[kLowRankMaxK];  // z = W^T x of a low-rank operator
   double L[kMaxM + 1];
   double coef[kMaxM + 1];
   double binom[kMaxM + 1];
@@ -185,7 +187,7 @@ __device__ __forceinline__ double spmv_row(const SelectArgs& a, const VT* __rest
 }  // namespace
 
 // Algorithm 1 on the team tm; a.part holds 2 x ceil(n / kChunk) partials and a.ctl is tm.ctl.
-template <typename VT>
+template <typename VT, bool LR = false>
 __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelShared& sh) {
   Ctl* ctl = tm.ctl;
   const int n = a.n, m = a.m;
@@ -210,8 +212,10 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
   double* V0 = a.Vb;
   {
     chunk_pass(n, tm, part, pc & 1, [&](long long row) {
-      const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
-      if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) bad = 1;
+      if (!LR) {
+        const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
+        if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) bad = 1;
+      }
       double x;
       if (a.v) {
         x = a.v[row];
@@ -262,8 +266,16 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
   // ---- guarded power basis ----------------------------------------------------------------------------
   for (int k = 1; k <= m && sh.go; ++k) {
     const double* __restrict__ Vp = a.Vb + vidx(k - 1, n, 0);
+    if constexpr (LR) {
+      const int r0 = (int)((long long)tm.rank * n / tm.size), r1 = (int)((long long)(tm.rank + 1) * n / tm.size);
+      if (!lr_reduce(tm, static_cast<const VT*>(a.lrW), a.lr_k, 1, r0, r1,
+                     [&](int row, int) { return Vp[(size_t)row * 2]; }, a.lr_part, sh.lz))
+        return;
+    }
     chunk_pass(n, tm, part, pc & 1, [&](long long row) {
-      const double y = spmv_row<VT>(a, vals, Vp, (int)row, bad);
+      double y;
+      if constexpr (LR) y = lr_row(static_cast<const VT*>(a.lrU), a.lr_k, (int)row, sh.lz, 1);
+      else y = spmv_row<VT>(a, vals, Vp, (int)row, bad);
       a.Vb[vidx(k, n, row)] = y;
       return y;
     });
@@ -318,8 +330,17 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
   for (int k = r + 1; k <= m; ++k) {
     const double* __restrict__ Vp = a.Vb + vidx(k - 1, n, 0);
     const double inv_s0 = sh.inv_s0;
-    for (long long row = first; row < n; row += stride)
-      a.Vb[vidx(k, n, row)] = spmv_row<VT>(a, vals, Vp, (int)row, bad) * inv_s0;
+    if constexpr (LR) {
+      const int r0 = (int)((long long)tm.rank * n / tm.size), r1 = (int)((long long)(tm.rank + 1) * n / tm.size);
+      if (!lr_reduce(tm, static_cast<const VT*>(a.lrW), a.lr_k, 1, r0, r1,
+                     [&](int row, int) { return Vp[(size_t)row * 2]; }, a.lr_part, sh.lz))
+        return;
+      for (long long row = first; row < n; row += stride)
+        a.Vb[vidx(k, n, row)] = lr_row(static_cast<const VT*>(a.lrU), a.lr_k, (int)row, sh.lz, 1) * inv_s0;
+    } else {
+      for (long long row = first; row < n; row += stride)
+        a.Vb[vidx(k, n, row)] = spmv_row<VT>(a, vals, Vp, (int)row, bad) * inv_s0;
+    }
     if (!team_sync(tm)) return;
   }
   // ---- Brent on f(xi) ---------------------------------------------------------------------------------

@@ -380,9 +380,46 @@ phic_csr device_csr(const Req* q) {
   return c;
 }
 
+// The requests of the next slice: every running request that has already taken part in a slice (its
+// per-slice work is bounded by max_steps), then new ones in arrival order while the estimated work,
+// spread over the launch's CTAs, stays within the slice budget (at least one request per slice).
+void pick_slice(phic_server& S) {
+  S.slice.clear();
+  double work = 0.0;  // estimated CTA-microseconds
+  // the budget grows with the backlog: short slices (latency) at light load, longer ones (throughput)
+  // when many requests wait
+  size_t fresh = 0;
+  for (const Req* q : S.running) fresh += q->slices == 0 ? 1 : 0;
+  const double scale = std::min(16.0, std::max(1.0, (double)(fresh + S.queued.size()) / 16.0));
+  const double budget = S.cfg.slice_us * scale * (double)S.grid;
+  const CostModel cm;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (Req* q : S.running) {
+      if ((int)S.slice.size() >= S.cfg.max_active) return;
+      const bool fresh = q->slices == 0;
+      if ((pass == 0) == fresh) continue;
+      phic_batch_item it;
+      std::memset(&it, 0, sizeof(it));
+      it.A.n = q->r.n;
+      it.A.prec = q->r.prec;
+      it.p = q->r.p;
+      it.r = q->r.r;
+      it.flags = q->selected ? 0u : PHIC_BATCH_SELECT;
+      it.s_hint = q->s_hint;
+      for (int j = 0; j < q->r.r; ++j) it.t[j] = q->r.t[j];
+      const long long want = (q->r.n + S.cfg.rows_per_cta - 1) / S.cfg.rows_per_cta;
+      const int team = (int)std::max<long long>(1, std::min<long long>(want, S.grid));
+      const double d = item_duration(it, S.sel_opts, team, fresh, cm) * team;
+      if (pass == 1 && !S.slice.empty() && work + d > budget) return;
+      work += d;
+      S.slice.push_back(q);
+    }
+  }
+}
+
 void start_slice(phic_server& S) {
-  const int k = (int)std::min<size_t>(S.running.size(), (size_t)S.cfg.max_active);
-  S.slice.assign(S.running.begin(), S.running.begin() + k);
+  pick_slice(S);
+  const int k = (int)S.slice.size();
   std::vector<phic_batch_item> items(k);
   std::vector<char> first(k);
   for (int i = 0; i < k; ++i) {
@@ -617,7 +654,8 @@ phic_status phic_server_create(const phic_server_config* cfg, phic_server** out)
   S->cfg = *cfg;
   if (S->cfg.rows_per_cta <= 0) S->cfg.rows_per_cta = 4096;
   if (S->cfg.blocks_per_sm <= 0) S->cfg.blocks_per_sm = 2;
-  if (S->cfg.max_steps <= 0) S->cfg.max_steps = 8;
+  if (S->cfg.max_steps <= 0) S->cfg.max_steps = 4;
+  if (!(S->cfg.slice_us > 0.0)) S->cfg.slice_us = 20000.0;
   if (S->cfg.max_active <= 0) S->cfg.max_active = 1024;
   if (S->cfg.m <= 0) S->cfg.m = 61;
   if (S->cfg.rows_per_cta < 256 || S->cfg.blocks_per_sm > 3 || S->cfg.m > 128) {

@@ -19,12 +19,31 @@ __global__ void __launch_bounds__(kBlock, MINB) recover_kernel(const SolveArgs a
   recover_body<T, CW>(a, tm, sm, phase, 0x7fffffff);
 }
 
+// Low-rank operators: the same bodies with A applied as U (W^T x) (one team reduction per product).
+template <typename T, int CW>
+__global__ void __launch_bounds__(kBlock, 2) lr_series_kernel(const SolveArgs a) {
+  __shared__ SeriesSmem<T> sm;
+  __shared__ LowRankSmem<T> lz;
+  Team tm = grid_team(a.ctlS, a.spin_ns);
+  int phase = 0;
+  series_body<T, CW, true>(a, tm, sm, phase, &lz);
+}
+
+template <typename T, int CW>
+__global__ void __launch_bounds__(kBlock, 2) lr_recover_kernel(const SolveArgs a) {
+  __shared__ RecoverSmem<T> sm;
+  __shared__ LowRankSmem<T> lz;
+  Team tm = grid_team(a.ctlR, a.spin_ns);
+  int phase = 0;
+  recover_body<T, CW, true>(a, tm, sm, phase, 0x7fffffff, &lz);
+}
+
 // ---------------------------------------------------------------------------------------------------
 namespace {
 
 template <typename K>
 cudaError_t coop_launch(K kernel, long long items, int max_per_sm, const SolveArgs& a, cudaStream_t st,
-                        int* grid_out) {
+                        int* grid_out, int max_grid = 1 << 30) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -39,6 +58,7 @@ cudaError_t coop_launch(K kernel, long long items, int max_per_sm, const SolveAr
   long long need = (items + kBlock - 1) / kBlock;
   long long grid = (long long)sms * per_sm;
   if (need < grid) grid = need < 1 ? 1 : need;
+  if (grid > max_grid) grid = max_grid;
   if (grid_out) *grid_out = (int)grid;
   void* args[] = {const_cast<SolveArgs*>(&a)};
   count_launch();
@@ -66,15 +86,49 @@ cudaError_t dispatch_recover_b(const SolveArgs& a, cudaStream_t st, int* g) {
   }
 }
 // Residency hint by tile width: 2 blocks per SM for tiles up to 4 columns, 3 for wider ones.
+// Resident blocks per SM the wide-tile kernels are built for (FP32 may take more: fewer registers).
+#ifndef PHIC_WIDE_MINB_F32
+#define PHIC_WIDE_MINB_F32 3
+#endif
+template <typename T>
+constexpr int wide_minb() { return sizeof(T) == 4 ? PHIC_WIDE_MINB_F32 : 3; }
 template <typename T>
 cudaError_t dispatch_series(const SolveArgs& a, cudaStream_t st, int* g) {
-  return a.S_lay.w <= 4 ? dispatch_series_b<T, 2>(a, st, g) : dispatch_series_b<T, 3>(a, st, g);
+  return a.S_lay.w <= 4 ? dispatch_series_b<T, 2>(a, st, g) : dispatch_series_b<T, wide_minb<T>()>(a, st, g);
 }
 template <typename T>
 cudaError_t dispatch_recover(const SolveArgs& a, cudaStream_t st, int* g) {
-  return a.F_lay.w <= 4 ? dispatch_recover_b<T, 2>(a, st, g) : dispatch_recover_b<T, 3>(a, st, g);
+  return a.F_lay.w <= 4 ? dispatch_recover_b<T, 2>(a, st, g) : dispatch_recover_b<T, wide_minb<T>()>(a, st, g);
 }
 }  // namespace
+
+template <typename T>
+cudaError_t dispatch_lr_series(const SolveArgs& a, cudaStream_t st) {
+  const long long items = (long long)a.n * a.S_lay.Lp2;
+  const int bps = blocks_per_sm(sizeof(T)) < 2 ? blocks_per_sm(sizeof(T)) : 2;
+  switch (a.S_lay.cw) {
+    case 1: return coop_launch(lr_series_kernel<T, 1>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+    case 2: return coop_launch(lr_series_kernel<T, 2>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+    default: return coop_launch(lr_series_kernel<T, 4>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+  }
+}
+template <typename T>
+cudaError_t dispatch_lr_recover(const SolveArgs& a, cudaStream_t st) {
+  const long long items = (long long)a.n * a.F_lay.Lp2;
+  const int bps = blocks_per_sm(sizeof(T)) < 2 ? blocks_per_sm(sizeof(T)) : 2;
+  switch (a.F_lay.cw) {
+    case 1: return coop_launch(lr_recover_kernel<T, 1>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+    case 2: return coop_launch(lr_recover_kernel<T, 2>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+    default: return coop_launch(lr_recover_kernel<T, 4>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+  }
+}
+
+cudaError_t launch_lr_series(const SolveArgs& a, int prec, cudaStream_t st) {
+  return prec == PHIC_F32 ? dispatch_lr_series<float>(a, st) : dispatch_lr_series<double>(a, st);
+}
+cudaError_t launch_lr_recover(const SolveArgs& a, int prec, cudaStream_t st) {
+  return prec == PHIC_F32 ? dispatch_lr_recover<float>(a, st) : dispatch_lr_recover<double>(a, st);
+}
 
 cudaError_t launch_series(const SolveArgs& a, int prec, cudaStream_t st, int* grid_out) {
   return prec == PHIC_F32 ? dispatch_series<float>(a, st, grid_out) : dispatch_series<double>(a, st, grid_out);

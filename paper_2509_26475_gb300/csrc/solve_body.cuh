@@ -34,6 +34,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "lowrank.cuh"
 
 // Tile shape of the block kernels: widest column chunk a lane takes (1, 2 or 4).  Two columns per lane
 // with two (narrow tiles) or three (tiles of 8 or more columns) resident blocks per SM measured fastest
@@ -133,10 +134,12 @@ __device__ __forceinline__ int scale_exponent(double ref) {
   return (ref > 0.0 && isfinite(ref)) ? ilogb(ref) : 0;
 }
 
-// Sum of products in the storage precision.  FP64: fused multiply-adds.  FP32: compensated (the
-// products' and sums' rounding errors are carried in a second FP32 word, error-free transformations
-// TwoProduct by FMA and TwoSum), so a row's sum is accurate to about one FP32 rounding whatever its
-// length; the FP32 path is memory-bound and these extra FP32 operations are free there.
+// Sum of products in the storage precision: fused multiply-adds.  The FP32 path can instead carry the
+// products' and sums' rounding errors in a second word (error-free transformations TwoProduct by FMA and
+// TwoSum; PHIC_F32_COMPENSATED=1).  With the per-step norm cap of FP32 solves (kTheta32) the rounding of
+// the Taylor terms dominates and the compensation changed no error measurably (max 1.13e-6 either way
+// over 128 FP32 instances against the FP64 oracle) while costing 14 % of the recovery term time, so it is
+// off by default.
 template <typename T>
 struct DotAcc {
   T hi;
@@ -145,7 +148,7 @@ struct DotAcc {
   __device__ __forceinline__ T value() const { return hi; }
 };
 #ifndef PHIC_F32_COMPENSATED
-#define PHIC_F32_COMPENSATED 1
+#define PHIC_F32_COMPENSATED 0
 #endif
 #if PHIC_F32_COMPENSATED
 template <>
@@ -327,6 +330,7 @@ struct RecoverScalars {
 };
 
 // Shared memory of the two bodies; a kernel that runs both keeps them in one union.
+// zs / zt: Z = W^T X of a low-rank operator (FP64 sums, and scaled in the tile type).
 template <typename T>
 struct SeriesSmem {
   SeriesScalars sc;
@@ -340,6 +344,11 @@ struct RecoverSmem {
   LoopCtl lc;
   WarpParts wp;
 };
+template <typename T>
+struct LowRankSmem {
+  double zs[kLowRankMaxE];
+  T zt[kLowRankMaxE];
+};
 
 // ===================================================================================================
 // Block series (Algorithm 3: setup and the first while loop)
@@ -351,8 +360,9 @@ struct RecoverSmem {
 //
 // Runs on the team tm; `phase` is the team's next slot phase (advanced by one per barrier).  Thread 0
 // of rank 0 records the outcome in a.state (status, s_int, term count, xi, s, eA, nodiag) on every exit.
-template <typename T, int CW>
-__device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSmem<T>& sm, int& phase) {
+template <typename T, int CW, bool LR = false>
+__device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSmem<T>& sm, int& phase,
+                                          LowRankSmem<T>* lz = nullptr) {
   SeriesScalars& sc = sm.sc;
   LoopCtl& lc = sm.lc;
   SeriesTerm<T>& tk = sm.tk;
@@ -431,47 +441,74 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   int bad = 0;
 
   // ---- setup pass 1: CSR checks, ||A - xi I||_inf, rows without a stored diagonal -------------------
-  {
-    const int ph = phase++;
-    slot_reset(tm, ph);
-    unsigned long long mx = 0, maxlen = 0;
-    int nodiag = 0;
-    for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
-      const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
-      if (row < br.r1 && lane == 0) {
-        const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
-        if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) {
-          bad = 1;
-        } else {
-          maxlen = (unsigned long long)(b1 - b0) > maxlen ? (unsigned long long)(b1 - b0) : maxlen;
-          bool shifted = false;
-          double rs = 0.0;
-          for (int q = b0; q < b1; ++q) {
-            const int col = __ldg(a.colidx + q);
-            if ((unsigned)col >= (unsigned)n) { bad = 1; continue; }
-            double v = (double)__ldg(vals + q);
-            if (!shifted && col == row) {
-              v -= sc.xi;
-              shifted = true;
+  if constexpr (!LR) {
+    {
+      const int ph = phase++;
+      slot_reset(tm, ph);
+      unsigned long long mx = 0, maxlen = 0;
+      int nodiag = 0;
+      for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
+        const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
+        if (row < br.r1 && lane == 0) {
+          const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
+          if (b1 < b0 || b0 < 0 || b1 > a.nnz || (row == 0 && b0 != 0) || (row == n - 1 && b1 != a.nnz)) {
+            bad = 1;
+          } else {
+            maxlen = (unsigned long long)(b1 - b0) > maxlen ? (unsigned long long)(b1 - b0) : maxlen;
+            bool shifted = false;
+            double rs = 0.0;
+            for (int q = b0; q < b1; ++q) {
+              const int col = __ldg(a.colidx + q);
+              if ((unsigned)col >= (unsigned)n) { bad = 1; continue; }
+              double v = (double)__ldg(vals + q);
+              if (!shifted && col == row) {
+                v -= sc.xi;
+                shifted = true;
+              }
+              rs += fabs(v);
             }
-            rs += fabs(v);
+            if (!shifted) rs += fabs(sc.xi);
+            a.rowflag[row] = shifted ? 0 : 1;
+            nodiag |= !shifted;
+            umax(mx, rs);
           }
-          if (!shifted) rs += fabs(sc.xi);
-          a.rowflag[row] = shifted ? 0 : 1;
-          nodiag |= !shifted;
-          umax(mx, rs);
         }
       }
+      warp_parts(wp, mx, (unsigned long long)nodiag, bad, 0, maxlen);
+      if (!team_sync_lead(tm, [&] { parts_to_slots(ctl, ph, wp); },
+                          [&] {
+                            const double na = slot_get(ctl, ph, 0);
+                            sc.eA = (na > 0.0 && isfinite(na)) ? ilogb(na) + 1 : 0;  // ||B||_inf < 1
+                            sc.nodiag = slot_get(ctl, ph, 1) != 0.0;
+                            // ELL copy of B when n times the longest row fits the copy's room
+                            const long long K = (long long)slot_raw(ctl, ph, 3);
+                            sc.ell = (K >= 1 && K <= 64 && K * (long long)n <= a.a1_cap) ? (int)K : 0;
+                            lc.status = read_status(ctl);
+                          }))
+        return PHIC_TIMEOUT;
     }
-    warp_parts(wp, mx, (unsigned long long)nodiag, bad, 0, maxlen);
+  } else {
+    // low-rank A = U W^T: ||A - xi I||_inf <= max_i sum_q |U_iq| sum_j |W_jq| + |xi|; no stored diagonal
+    const int ph = phase++;
+    slot_reset(tm, ph);
+    const T* __restrict__ U = static_cast<const T*>(a.lrU);
+    const T* __restrict__ Wl = static_cast<const T*>(a.lrW);
+    const int k = a.lr_k;
+    if (!lr_reduce(tm, Wl, k, 1, br.r0, br.r1, [](int, int) { return 1.0; }, a.lr_part, lz->zs, true))
+      return PHIC_TIMEOUT;
+    unsigned long long mx = 0;
+    for (int row = br.r0 + (int)threadIdx.x; row < br.r1; row += kBlock) {
+      double rs = fabs(sc.xi);
+      for (int q = 0; q < k; ++q) rs += fabs((double)U[(size_t)row * k + q]) * lz->zs[q];
+      umax(mx, rs);
+    }
+    warp_parts(wp, mx, 1ull, 0);
     if (!team_sync_lead(tm, [&] { parts_to_slots(ctl, ph, wp); },
                         [&] {
                           const double na = slot_get(ctl, ph, 0);
-                          sc.eA = (na > 0.0 && isfinite(na)) ? ilogb(na) + 1 : 0;  // ||B||_inf < 1
-                          sc.nodiag = slot_get(ctl, ph, 1) != 0.0;
-                          // ELL copy of B when n times the longest row fits the copy's room
-                          const long long K = (long long)slot_raw(ctl, ph, 3);
-                          sc.ell = (K >= 1 && K <= 64 && K * (long long)n <= a.a1_cap) ? (int)K : 0;
+                          sc.eA = (na > 0.0 && isfinite(na)) ? ilogb(na) + 1 : 0;
+                          sc.nodiag = 1;  // the shift is applied to every row explicitly
+                          sc.ell = 0;
                           lc.status = read_status(ctl);
                         }))
       return PHIC_TIMEOUT;
@@ -491,7 +528,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
       const bool act = row < br.r1 && lane < L.L;
       T part = T(0);
       if (act) {
-        if (lane == 0) {
+        if (!LR && lane == 0) {
           const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
           const int K = sc.ell;
           bool shifted = false;
@@ -588,6 +625,14 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
     T* __restrict__ Vn = static_cast<T*>(a.Vt[kk & 1]);
     const T* __restrict__ Do = static_cast<const T*>(a.Dt[(kk - 1) & 1]);
     T* __restrict__ Dn = static_cast<T*>(a.Dt[kk & 1]);
+    if constexpr (LR) {  // Z = W^T D 2^-eA for this term's products
+      if (!lr_reduce(tm, static_cast<const T*>(a.lrW), a.lr_k, L.w, br.r0, br.r1,
+                     [&](int row, int c) { return (double)Do[(size_t)row * L.ws + c]; }, a.lr_part, lz->zs))
+        return PHIC_TIMEOUT;
+      const double scaleB = ldexp(1.0, -sc.eA);
+      for (int e = threadIdx.x; e < a.lr_k * L.w; e += kBlock) lz->zt[e] = (T)(lz->zs[e] * scaleB);
+      __syncthreads();
+    }
     unsigned long long mD = 0, mS = 0;
     const int bias = lc.bias;
     const float fscale = lc.fscale;
@@ -601,8 +646,14 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
         T acc[CW];
 #pragma unroll
         for (int j = 0; j < CW; ++j) acc[j] = T(0);
-        spmm_row<T, CW>(rowptr, ent, n, ell, Do, L.ws, c0, row, acc);
-        if (nodiag && rowflag[row]) {  // no stored diagonal: apply the shift explicitly
+        if constexpr (LR) {
+#pragma unroll
+          for (int j = 0; j < CW; ++j)
+            acc[j] = kLive[j] ? lr_row(static_cast<const T*>(a.lrU), a.lr_k, row, lz->zt + c0 + j, L.w) : T(0);
+        } else {
+          spmm_row<T, CW>(rowptr, ent, n, ell, Do, L.ws, c0, row, acc);
+        }
+        if (nodiag && (LR || rowflag[row])) {  // no stored diagonal: apply the shift explicitly
           T own[CW];
           VecIO<T, CW>::ld(Do + o, own);
 #pragma unroll
@@ -649,9 +700,10 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   return lc.status;
 }
 
-template <typename T, int CW>
-__device__ __forceinline__ void series_body(const SolveArgs& a, Team& tm, SeriesSmem<T>& sm, int& phase) {
-  int st = series_run<T, CW>(a, tm, sm, phase);
+template <typename T, int CW, bool LR = false>
+__device__ __forceinline__ void series_body(const SolveArgs& a, Team& tm, SeriesSmem<T>& sm, int& phase,
+                                            LowRankSmem<T>* lz = nullptr) {
+  int st = series_run<T, CW, LR>(a, tm, sm, phase, lz);
   if (tm.rank == 0 && threadIdx.x == 0) {
     if (st != PHIC_OK) set_status(tm.ctl, st);
     SolveState* sv = a.state;
@@ -697,9 +749,9 @@ __device__ __forceinline__ void jt_power_coeffs(RecoverScalars<T>& rs, const Sol
 // max_steps outer steps j; it writes the output once j reaches s_int - 1, and otherwise records in
 // a.state where the next slice resumes.  Returns 1 once the solve is finished (output written or an
 // error recorded).
-template <typename T, int CW>
+template <typename T, int CW, bool LR = false>
 __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, RecoverSmem<T>& sm, int& phase,
-                                            int max_steps) {
+                                            int max_steps, LowRankSmem<T>* lz = nullptr) {
   RecoverScalars<T>& sc = sm.sc;
   LoopCtl& lc = sm.lc;
   WarpParts& wp = sm.wp;
@@ -796,6 +848,15 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
 
   // ---- F = S(:, [blk 0, blk p]);  F(:,1:r) <- A F(:,1:r) T + v0 1^T (unshifted A, t undivided) -----
   if (!sc.rec_init) {
+    if constexpr (LR) {  // Z = W^T S(:, blk 0) for the unshifted product A F(:, 1:r)
+      if (!lr_reduce(tm, static_cast<const T*>(a.lrW), a.lr_k, r, br.r0, br.r1,
+                     [&](int row, int c) { return (double)S[(size_t)row * ws_s + c]; }, a.lr_part, lz->zs)) {
+        finish(PHIC_TIMEOUT);
+        return 1;
+      }
+      for (int e = threadIdx.x; e < a.lr_k * r; e += kBlock) lz->zt[e] = (T)lz->zs[e];
+      __syncthreads();
+    }
     const int ph = phase++;
     slot_reset(tm, ph);
     T* F = static_cast<T*>(a.Ft[0]);
@@ -813,11 +874,15 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
           if (kLive[j] && !kBlkP[j]) {
             const int i = kI[j];
             T acc = T(0);
-            const int beg = __ldg(a.rowptr + row), end = __ldg(a.rowptr + row + 1);
-            for (int q = beg; q < end; ++q) {
-              const int col = __ldg(a.colidx + q);
-              if ((unsigned)col >= (unsigned)n) { bad = 1; continue; }
-              acc = fma(__ldg(vals + q), S[(size_t)col * ws_s + i], acc);
+            if constexpr (LR) {
+              acc = lr_row(static_cast<const T*>(a.lrU), a.lr_k, row, lz->zt + i, r);
+            } else {
+              const int beg = __ldg(a.rowptr + row), end = __ldg(a.rowptr + row + 1);
+              for (int q = beg; q < end; ++q) {
+                const int col = __ldg(a.colidx + q);
+                if ((unsigned)col >= (unsigned)n) { bad = 1; continue; }
+                acc = fma(__ldg(vals + q), S[(size_t)col * ws_s + i], acc);
+              }
             }
             v = fma(acc, kTt[j], v0 ? v0[row] : T(0));
           } else if (kBlkP[j]) {
@@ -905,6 +970,16 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
       }
       const T* __restrict__ Go = static_cast<const T*>(a.Ft[cur]);
       T* __restrict__ Gn = static_cast<T*>(a.Ft[cur ^ 1]);
+      if constexpr (LR) {  // Z = W^T G 2^-eA for this term's products
+        if (!lr_reduce(tm, static_cast<const T*>(a.lrW), a.lr_k, L.w, br.r0, br.r1,
+                       [&](int row, int c) { return (double)Go[(size_t)row * L.ws + c]; }, a.lr_part, lz->zs)) {
+          finish(PHIC_TIMEOUT);
+          return 1;
+        }
+        const double scaleB = ldexp(1.0, -sc.eA);
+        for (int e = threadIdx.x; e < a.lr_k * L.w; e += kBlock) lz->zt[e] = (T)(lz->zs[e] * scaleB);
+        __syncthreads();
+      }
       unsigned long long mF = 0, mE = 0;
       const int bias = lc.bias;
       const float fscale = lc.fscale;
@@ -915,9 +990,15 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
         float pF = 0.f, pE = 0.f;
         if (act) {
           T acc[CW];
-          spmm_row<T, CW>(rowptr, ent, n, ell, Go, L.ws, c0, row, acc);
+          if constexpr (LR) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j)
+              acc[j] = kLive[j] ? lr_row(static_cast<const T*>(a.lrU), a.lr_k, row, lz->zt + c0 + j, L.w) : T(0);
+          } else {
+            spmm_row<T, CW>(rowptr, ent, n, ell, Go, L.ws, c0, row, acc);
+          }
           const size_t o = (size_t)row * L.ws + c0;
-          const bool shift_row = nodiag && rowflag[row];
+          const bool shift_row = nodiag && (LR || rowflag[row]);
           T e[CW];
           if (kk == 1 || shift_row) {
             T own[CW];

@@ -176,3 +176,35 @@ def low_rank_comb(U, M, V, t):
         out += V[j] / math.factorial(j)
         inner += ph[j + 1] @ (W.T @ V[j])
     return out + U @ (float(t) * inner)
+
+
+def phi_matrices_ld(X, upto: int):
+    """[phi_0(X), ..., phi_upto(X)] for a small square X from the long-double exponential of the same
+    block matrix as phi_matrices (no mpmath: usable where only numpy is installed)."""
+    X = np.asarray(X, dtype=np.float64)
+    k = X.shape[0]
+    B = upto + 1
+    Big = np.zeros((k * B, k * B), dtype=np.longdouble)
+    Big[:k, :k] = X
+    for q in range(B - 1):
+        for a in range(k):
+            Big[q * k + a, (q + 1) * k + a] = 1
+    E = expm_longdouble(Big)
+    return [E[:k, q * k:(q + 1) * k] for q in range(B)]
+
+
+def low_rank_comb_ld(U, W, M, V, t, alpha=1.0):
+    """sum_j alpha^j phi_j(tA) v_j for A = U W^T with W = U M^T:
+    sum_j alpha^j v_j/j! + U (t sum_j alpha^j phi_{j+1}(tM) W^T v_j), in long double."""
+    p = V.shape[0] - 1
+    ph = phi_matrices_ld(float(t) * np.asarray(M), p + 1)
+    Ul = np.asarray(U, dtype=np.longdouble)
+    Wl = np.asarray(W, dtype=np.longdouble)
+    Vl = np.asarray(V, dtype=np.longdouble)
+    a = np.longdouble(alpha)
+    out = np.zeros(U.shape[0], dtype=np.longdouble)
+    inner = np.zeros(U.shape[1], dtype=np.longdouble)
+    for j in range(p + 1):
+        out += a**j * Vl[j] / math.factorial(j)
+        inner += a**j * (ph[j + 1] @ (Wl.T @ Vl[j]))
+    return (out + Ul @ (np.longdouble(t) * inner)).astype(np.float64)

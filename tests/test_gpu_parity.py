@@ -175,10 +175,14 @@ def test_advdiff2d_1024_full_size_fp64_and_fp32(oracle_mod):
     W, gst = _gpu_solve(w["A"], w["V"], w["t"], w["alpha"], TOL53, sel["s"], sel["xi"])
     assert gst["status"] == 0 and gst["s_int"] == ost["s_int"] > 1
     assert max(_rel(W, ref)) <= 1e-12
-    # FP32 with the parameters Algorithm 1 picks for tol = 2^-24; the exact result does not depend on
-    # (s, xi), so the FP64 oracle result above is the reference
-    sel24 = oracle_mod.select(w["A"], tol=TOL24)
-    W32, g32 = _gpu_solve(w["A"], w["V"], w["t"], w["alpha"], TOL24, sel24["s"], sel24["xi"], dtype=torch.float32)
+    # FP32 with the GPU's Algorithm 1 for tol = 2^-24 (its s0 and f* let the FP32 solve cap each step's
+    # norm); the exact result does not depend on (s, xi), so the FP64 oracle result above is the reference
+    A32 = api.DeviceCSR.from_host(w["A"], dtype=torch.float32)
+    P32 = api.select_params(A32, tol=TOL24)
+    W32d, st32 = api.solve(A32, torch.as_tensor(w["V"]).float().cuda(), w["t"], w["alpha"], TOL24, P32)
+    torch.cuda.synchronize()
+    g32 = api.read_stats(st32)
+    W32 = W32d.cpu().numpy()
     assert g32["status"] == 0
     assert max(_rel(W32, ref)) <= 5e-6
     print(f"advdiff 1024^2 h=1e-5: fp64 errs={_rel(W, ref)} fp32 errs={_rel(W32, ref)} s_int={gst['s_int']}")
