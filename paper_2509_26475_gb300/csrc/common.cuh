@@ -17,7 +17,9 @@ struct __align__(256) Ctl {
   int status;              // first phic_status != OK seen by any block
   int fault;               // unused padding kept for layout stability
   unsigned long long slot[4][4];  // max-reduction slots (bit patterns of non-negative values), by phase % 4
-  double pad[13];
+  int dia_keys[16];        // set of the operator's diagonal offsets (offset + n; 0 = empty), hashed
+  int dia_ovf;             // more than 16 distinct offsets
+  int pad[9];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte line");
 

@@ -35,7 +35,8 @@ struct SolveState {
   int max_inner;
   int done;       // 1 once the output has been written
   int ell;        // copy of B: ELL with this many slots per row, or 0 for CSR order
-  int pad;
+  int ndia;       // copy of B: DIA with these diagonals (ndia > 0; takes precedence over ell)
+  int dia_off[16];
 };
 
 // Entry of the solve's copy of A_1 = A - xi I, scaled by 2^-eA: column and value in one aligned load.

@@ -250,10 +250,73 @@ __device__ __forceinline__ void spmm_ell_dyn(const CsrEnt<T>* __restrict__ ent, 
   for (int j = 0; j < CW; ++j) acc[j] = d[j].value();
 }
 
+// The same over the DIA copy of B: the value of diagonal d (offset off[d]) in `row` at val[d n + row]
+// (zero where the row has no entry on it).  The gathered rows row + off[d] follow from the offsets, so
+// every load of a row is issued at once and consecutive rows read consecutive memory.  Columns outside
+// [0, n) carry a zero value and are read from the row itself.
+template <typename T, int CW, int D>
+__device__ __forceinline__ void spmm_dia_k(const T* __restrict__ val, const int (&off)[7], int n,
+                                           const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW]) {
+  T v[D];
+  T x[D][CW];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int j = row + off[d];
+    const int jj = (unsigned)j < (unsigned)n ? j : row;
+    v[d] = val[(size_t)d * n + row];
+    VecIO<T, CW>::ld(X + (size_t)jj * ws + c0, x[d]);
+  }
+  DotAcc<T> acc_d[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc_d[c].zero();
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc_d[c].add(v[d], x[d][c]);
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc[c] = acc_d[c].value();
+}
+
+template <typename T, int CW>
+__device__ __forceinline__ void spmm_dia_dyn(const T* __restrict__ val, const int* off, int D, int n,
+                                             const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW]) {
+  DotAcc<T> acc_d[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc_d[c].zero();
+  for (int d = 0; d < D; ++d) {
+    const int j = row + off[d];
+    const int jj = (unsigned)j < (unsigned)n ? j : row;
+    const T v = val[(size_t)d * n + row];
+    T x[CW];
+    VecIO<T, CW>::ld(X + (size_t)jj * ws + c0, x);
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc_d[c].add(v, x[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc[c] = acc_d[c].value();
+}
+
+// Diagonal offsets of the DIA copy kept in registers for the widths with fixed loops (5 and 7).
+struct DiaOffsets {
+  int o[7];
+  __device__ __forceinline__ void load(const int* off, int D) {
+#pragma unroll
+    for (int d = 0; d < 7; ++d) o[d] = d < D ? off[d] : 0;
+  }
+};
+
 // B X for one row through whichever copy of B the setup built (ell = K > 0: ELL with K slots; 0: CSR).
 template <typename T, int CW>
 __device__ __forceinline__ void spmm_row(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent, int n,
-                                         int ell, const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW]) {
+                                         int ell, const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW],
+                                         int ndia = 0, const DiaOffsets* dor = nullptr, const int* doff = nullptr) {
+  if (ndia) {
+    const T* __restrict__ val = reinterpret_cast<const T*>(ent);
+    if (ndia == 5) spmm_dia_k<T, CW, 5>(val, dor->o, n, X, ws, c0, row, acc);
+    else if (ndia == 7) spmm_dia_k<T, CW, 7>(val, dor->o, n, X, ws, c0, row, acc);
+    else spmm_dia_dyn<T, CW>(val, doff, ndia, n, X, ws, c0, row, acc);
+    return;
+  }
   switch (ell) {
     case 0: spmm_ent<T, CW>(rowptr, ent, X, ws, c0, row, acc); break;
     case 5: spmm_ell_k<T, CW, 5>(ent, n, X, ws, c0, row, acc); break;
@@ -315,7 +378,8 @@ constexpr double kTheta32 = 8.317766166719343;
 
 struct SeriesScalars {
   double xi, s_used, tc[PHIC_MAX_R], cA[PHIC_MAX_R], cD[PHIC_MAX_R], cV[PHIC_MAX_R];
-  int s_int, bad, eA, nodiag, ell;
+  int s_int, bad, eA, nodiag, ell, ndia;
+  int dia_off[16];
 };
 
 template <typename T>
@@ -324,7 +388,8 @@ struct RecoverScalars {
   T coef[PHIC_MAX_R];
   float fcoef[PHIC_MAX_R];
   T cj[PHIC_MAX_P + 1][PHIC_MAX_R];
-  int s_int, series_terms, status, eA, nodiag, ell;
+  int s_int, series_terms, status, eA, nodiag, ell, ndia;
+  int dia_off[16];
   int done, rec_init, j_done, cur;
   double cF0;
 };
@@ -404,6 +469,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
     sc.eA = 0;
     sc.nodiag = 0;
     sc.ell = 0;
+    sc.ndia = 0;
     lc.k = 1;
   }
   __syncthreads();
@@ -447,6 +513,26 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
       slot_reset(tm, ph);
       unsigned long long mx = 0, maxlen = 0;
       int nodiag = 0;
+      // the distinct diagonal offsets (col - row) of the stored entries, as keys offset + n in a block-wide
+      // hash table, then merged into the team's 16-entry table in the control block
+      __shared__ int s_dkeys[32];
+      __shared__ int s_dovf;
+      if (threadIdx.x < 32) s_dkeys[threadIdx.x] = 0;
+      if (threadIdx.x == 0) s_dovf = 0;
+      __syncthreads();
+      auto dia_insert = [&](int key) {
+        int h = key & 31;
+        for (int probe = 0; probe < 32; ++probe) {
+          const int cur = *(volatile int*)&s_dkeys[h];
+          if (cur == key) return;
+          if (cur == 0) {
+            const int old = atomicCAS(&s_dkeys[h], 0, key);
+            if (old == 0 || old == key) return;
+          }
+          h = (h + 1) & 31;
+        }
+        s_dovf = 1;
+      };
       for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
         const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
         if (row < br.r1 && lane == 0) {
@@ -460,6 +546,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
             for (int q = b0; q < b1; ++q) {
               const int col = __ldg(a.colidx + q);
               if ((unsigned)col >= (unsigned)n) { bad = 1; continue; }
+              dia_insert(col - row + n);
               double v = (double)__ldg(vals + q);
               if (!shifted && col == row) {
                 v -= sc.xi;
@@ -475,14 +562,44 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
         }
       }
       warp_parts(wp, mx, (unsigned long long)nodiag, bad, 0, maxlen);
+      __syncthreads();
+      if (threadIdx.x < 32) {  // merge this block's offsets into the team's table
+        const int key = s_dkeys[threadIdx.x];
+        if (key != 0) {
+          int h = key & 15, probe = 0;
+          for (; probe < 16; ++probe) {
+            const int old = atomicCAS(&ctl->dia_keys[h], 0, key);
+            if (old == 0 || old == key) break;
+            h = (h + 1) & 15;
+          }
+          if (probe == 16) atomicOr(&ctl->dia_ovf, 1);
+        }
+        if (threadIdx.x == 0 && s_dovf) atomicOr(&ctl->dia_ovf, 1);
+      }
       if (!team_sync_lead(tm, [&] { parts_to_slots(ctl, ph, wp); },
                           [&] {
                             const double na = slot_get(ctl, ph, 0);
                             sc.eA = (na > 0.0 && isfinite(na)) ? ilogb(na) + 1 : 0;  // ||B||_inf < 1
                             sc.nodiag = slot_get(ctl, ph, 1) != 0.0;
-                            // ELL copy of B when n times the longest row fits the copy's room
+                            // DIA copy of B when its diagonals are few and fill the rows well; else ELL
+                            // when n times the longest row fits the copy's room; else CSR order
+                            int nd = 0;
+                            for (int q = 0; q < 16; ++q) {
+                              const int key = *(volatile const int*)&ctl->dia_keys[q];
+                              if (key != 0) sc.dia_off[nd++] = key - n;
+                            }
+                            for (int q = 1; q < nd; ++q)  // ascending offsets
+                              for (int u = q; u > 0 && sc.dia_off[u - 1] > sc.dia_off[u]; --u) {
+                                const int tmp = sc.dia_off[u];
+                                sc.dia_off[u] = sc.dia_off[u - 1];
+                                sc.dia_off[u - 1] = tmp;
+                              }
+                            const bool ovf = *(volatile const int*)&ctl->dia_ovf != 0;
+                            const long long cells = (long long)nd * n;
+                            sc.ndia = (!ovf && nd >= 1 && cells <= 2 * a.a1_cap &&
+                                       cells <= (long long)a.nnz + a.nnz / 2 + 64) ? nd : 0;
                             const long long K = (long long)slot_raw(ctl, ph, 3);
-                            sc.ell = (K >= 1 && K <= 64 && K * (long long)n <= a.a1_cap) ? (int)K : 0;
+                            sc.ell = (!sc.ndia && K >= 1 && K <= 64 && K * (long long)n <= a.a1_cap) ? (int)K : 0;
                             lc.status = read_status(ctl);
                           }))
         return PHIC_TIMEOUT;
@@ -509,6 +626,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
                           sc.eA = (na > 0.0 && isfinite(na)) ? ilogb(na) + 1 : 0;
                           sc.nodiag = 1;  // the shift is applied to every row explicitly
                           sc.ell = 0;
+                          sc.ndia = 0;
                           lc.status = read_status(ctl);
                         }))
       return PHIC_TIMEOUT;
@@ -528,7 +646,26 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
       const bool act = row < br.r1 && lane < L.L;
       T part = T(0);
       if (act) {
-        if (!LR && lane == 0) {
+        if (!LR && lane == 0 && sc.ndia) {  // DIA: per-diagonal sums in FP64, xi subtracted once
+          const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
+          const int D = sc.ndia;
+          double dsum[16];
+          for (int d = 0; d < D; ++d) dsum[d] = 0.0;
+          bool shifted = false;
+          for (int q = b0; q < b1; ++q) {
+            const int col = __ldg(a.colidx + q);
+            double v = (double)__ldg(vals + q);
+            if (!shifted && col == row) {
+              v -= sc.xi;
+              shifted = true;
+            }
+            int d = 0;
+            while (d < D - 1 && sc.dia_off[d] != col - row) ++d;
+            dsum[d] += v;
+          }
+          T* __restrict__ dval = reinterpret_cast<T*>(a.A1);
+          for (int d = 0; d < D; ++d) dval[(size_t)d * n + row] = (T)(dsum[d] * scaleB);
+        } else if (!LR && lane == 0) {
           const int b0 = __ldg(a.rowptr + row), b1 = __ldg(a.rowptr + row + 1);
           const int K = sc.ell;
           bool shifted = false;
@@ -610,6 +747,9 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   const int* __restrict__ rowptr = a.rowptr;
   const unsigned char* __restrict__ rowflag = a.rowflag;
   const int ell = sc.ell;
+  const int ndia = sc.ndia;
+  DiaOffsets dor;
+  dor.load(sc.dia_off, ndia);
   while (lc.go) {
     const int kk = lc.k;
     const int ph = phase++;
@@ -651,7 +791,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
           for (int j = 0; j < CW; ++j)
             acc[j] = kLive[j] ? lr_row(static_cast<const T*>(a.lrU), a.lr_k, row, lz->zt + c0 + j, L.w) : T(0);
         } else {
-          spmm_row<T, CW>(rowptr, ent, n, ell, Do, L.ws, c0, row, acc);
+          spmm_row<T, CW>(rowptr, ent, n, ell, Do, L.ws, c0, row, acc, ndia, &dor, sc.dia_off);
         }
         if (nodiag && (LR || rowflag[row])) {  // no stored diagonal: apply the shift explicitly
           T own[CW];
@@ -722,6 +862,8 @@ __device__ __forceinline__ void series_body(const SolveArgs& a, Team& tm, Series
     sv->max_inner = 0;
     sv->done = 0;
     sv->ell = sm.sc.ell;
+    sv->ndia = sm.sc.ndia;
+    for (int d = 0; d < 16; ++d) sv->dia_off[d] = d < sm.sc.ndia ? sm.sc.dia_off[d] : 0;
   }
 }
 
@@ -770,6 +912,8 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
     sc.eA = vs->eA;
     sc.nodiag = vs->nodiag;
     sc.ell = vs->ell;
+    sc.ndia = vs->ndia;
+    for (int d = 0; d < 16; ++d) sc.dia_off[d] = vs->dia_off[d];
     sc.done = vs->done;
     sc.rec_init = vs->rec_init;
     sc.j_done = vs->j_done;
@@ -919,6 +1063,9 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   const double tol = a.tol;
   const int max_terms = a.max_terms;
   const int ell = sc.ell;
+  const int ndia = sc.ndia;
+  DiaOffsets dor;
+  dor.load(sc.dia_off, ndia);
 
   // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||: next term
   auto decide = [&]() {
@@ -995,7 +1142,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
             for (int j = 0; j < CW; ++j)
               acc[j] = kLive[j] ? lr_row(static_cast<const T*>(a.lrU), a.lr_k, row, lz->zt + c0 + j, L.w) : T(0);
           } else {
-            spmm_row<T, CW>(rowptr, ent, n, ell, Go, L.ws, c0, row, acc);
+            spmm_row<T, CW>(rowptr, ent, n, ell, Go, L.ws, c0, row, acc, ndia, &dor, sc.dia_off);
           }
           const size_t o = (size_t)row * L.ws + c0;
           const bool shift_row = nodiag && (LR || rowflag[row]);
