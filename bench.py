@@ -123,19 +123,28 @@ def torch_dtype():
     return torch.float64 if PRECISION == "f64" else torch.float32
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu record, if that record was
-    taken on the current kernel source (sha256 of solve.cu); None otherwise."""
+def recorded_traffic(terms: int):
+    """DRAM bytes of one launch of the dominant kernel from the committed ncu record of this workload and
+    precision, if that record was taken on the current kernel source (sha256); None otherwise.  A record
+    of a shorter launch of the same kernel (fewer Taylor terms) is scaled by the terms: every term moves
+    the same bytes once the working set exceeds L2, which is when the scaling is used."""
     import hashlib
 
+    name = "recover_kernel_convdiff3d_64.json" if (WORKLOAD, PRECISION) == ("convdiff3d-64", "f64") else \
+        "recover_kernel_advdiff2d_1024_fp32.json" if (WORKLOAD, PRECISION) == ("advdiff2d-1024", "f32") else None
+    if name is None:
+        return None
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "recover_kernel_convdiff3d_64.json")))
+        rec = json.load(open(os.path.join(ROOT, "profiles", name)))
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() == rec["sha256"]:
-            return float(rec["dram_bytes_per_launch"])
+        if hashlib.sha256(src).hexdigest() != rec["sha256"]:
+            return None
+        b = float(rec["dram_bytes_per_launch"])
+        if "terms_per_launch" in rec:
+            b *= terms / float(rec["terms_per_launch"])
+        return b
     except Exception:
-        pass
-    return None
+        return None
 
 
 def reduce_max_over_ranks(x: float, dist, device) -> float:
@@ -381,14 +390,14 @@ def main():
         roofline = {"bound": "alu", "kernel": kernel,
                     "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
                     "frac": achieved / FP64_PEAK_GOPS,
-                    "traffic": recorded_traffic() if WORKLOAD == "convdiff3d-64" else None,
+                    "traffic": recorded_traffic(st_last["recovery_terms"]),
                     "peak_note": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (probe measured 1.91 FMA/clk/SM)",
                     "launch_ms": statistics.mean(rec_ms), "terms_per_launch": st_last["recovery_terms"],
                     "hbm_view": {"algorithmic_gbs": hbm_gbs, "peak_gbs": hbm_peak,
                                  "frac_of_measured": hbm_gbs / hbm_peak}}
     else:
         roofline = {"bound": "hbm", "kernel": kernel, "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_gbs / hbm_peak, "traffic": None,
+                    "frac": hbm_gbs / hbm_peak, "traffic": recorded_traffic(st_last["recovery_terms"]),
                     "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured)",
                     "launch_ms": statistics.mean(rec_ms), "terms_per_launch": st_last["recovery_terms"]}
 
