@@ -50,6 +50,9 @@ template <>
 __device__ __forceinline__ void run_series<float>(const SolveArgs& a, Team& tm, BatchSmem& u, int& phase) {
   if (a.S_lay.cw == 1) series_call<float, 1>(a, tm, u.s32, phase);
   else if (a.S_lay.cw == 2) series_call<float, 2>(a, tm, u.s32, phase);
+#if PHIC_CW_MAX_F32 >= 8
+  else if (a.S_lay.cw == 8) series_call<float, 8>(a, tm, u.s32, phase);
+#endif
   else series_call<float, 4>(a, tm, u.s32, phase);
 }
 
@@ -66,6 +69,9 @@ __device__ __forceinline__ void run_recover<float>(const SolveArgs& a, Team& tm,
                                                     int steps) {
   if (a.F_lay.cw == 1) recover_call<float, 1>(a, tm, u.r32, phase, steps);
   else if (a.F_lay.cw == 2) recover_call<float, 2>(a, tm, u.r32, phase, steps);
+#if PHIC_CW_MAX_F32 >= 8
+  else if (a.F_lay.cw == 8) recover_call<float, 8>(a, tm, u.r32, phase, steps);
+#endif
   else recover_call<float, 4>(a, tm, u.r32, phase, steps);
 }
 

@@ -285,6 +285,20 @@ struct VecIO<float, 4> {
   }
 };
 
+template <>
+struct VecIO<float, 8> {
+  static __device__ __forceinline__ void ld(const float* p, float (&x)[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    const float4 b = reinterpret_cast<const float4*>(p)[1];
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+  }
+  static __device__ __forceinline__ void st(float* p, const float (&x)[8]) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(x[0], x[1], x[2], x[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(x[4], x[5], x[6], x[7]);
+  }
+};
+
 // Sum over the lanes of one row group (Lp2 consecutive lanes, a power of two <= 32, aligned).
 template <typename T>
 __device__ __forceinline__ T group_sum(T v, int Lp2) {

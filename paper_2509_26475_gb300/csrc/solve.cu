@@ -72,6 +72,11 @@ cudaError_t dispatch_series_b(const SolveArgs& a, cudaStream_t st, int* g) {
   switch (a.S_lay.cw) {
     case 1: return coop_launch(series_kernel<T, 1, MINB>, items, bps, a, st, g);
     case 2: return coop_launch(series_kernel<T, 2, MINB>, items, bps, a, st, g);
+#if PHIC_CW_MAX_F32 >= 8
+    case 8:
+      if constexpr (sizeof(T) == 4) return coop_launch(series_kernel<T, 8, MINB>, items, bps, a, st, g);
+      return cudaErrorInvalidValue;
+#endif
     default: return coop_launch(series_kernel<T, 4, MINB>, items, bps, a, st, g);
   }
 }
@@ -82,16 +87,24 @@ cudaError_t dispatch_recover_b(const SolveArgs& a, cudaStream_t st, int* g) {
   switch (a.F_lay.cw) {
     case 1: return coop_launch(recover_kernel<T, 1, MINB>, items, bps, a, st, g);
     case 2: return coop_launch(recover_kernel<T, 2, MINB>, items, bps, a, st, g);
+#if PHIC_CW_MAX_F32 >= 8
+    case 8:
+      if constexpr (sizeof(T) == 4) return coop_launch(recover_kernel<T, 8, MINB>, items, bps, a, st, g);
+      return cudaErrorInvalidValue;
+#endif
     default: return coop_launch(recover_kernel<T, 4, MINB>, items, bps, a, st, g);
   }
 }
 // Residency hint by tile width: 2 blocks per SM for tiles up to 4 columns, 3 for wider ones.
-// Resident blocks per SM the wide-tile kernels are built for (FP32 may take more: fewer registers).
+// Resident blocks per SM the wide-tile kernels (more than 4 columns) are built for.
 #ifndef PHIC_WIDE_MINB_F32
 #define PHIC_WIDE_MINB_F32 3
 #endif
+#ifndef PHIC_WIDE_MINB_F64
+#define PHIC_WIDE_MINB_F64 3
+#endif
 template <typename T>
-constexpr int wide_minb() { return sizeof(T) == 4 ? PHIC_WIDE_MINB_F32 : 3; }
+constexpr int wide_minb() { return sizeof(T) == 4 ? PHIC_WIDE_MINB_F32 : PHIC_WIDE_MINB_F64; }
 template <typename T>
 cudaError_t dispatch_series(const SolveArgs& a, cudaStream_t st, int* g) {
   return a.S_lay.w <= 4 ? dispatch_series_b<T, 2>(a, st, g) : dispatch_series_b<T, wide_minb<T>()>(a, st, g);
@@ -109,6 +122,11 @@ cudaError_t dispatch_lr_series(const SolveArgs& a, cudaStream_t st) {
   switch (a.S_lay.cw) {
     case 1: return coop_launch(lr_series_kernel<T, 1>, items, bps, a, st, nullptr, kLowRankMaxGrid);
     case 2: return coop_launch(lr_series_kernel<T, 2>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+#if PHIC_CW_MAX_F32 >= 8
+    case 8:
+      if constexpr (sizeof(T) == 4) return coop_launch(lr_series_kernel<T, 8>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+      return cudaErrorInvalidValue;
+#endif
     default: return coop_launch(lr_series_kernel<T, 4>, items, bps, a, st, nullptr, kLowRankMaxGrid);
   }
 }
@@ -119,6 +137,11 @@ cudaError_t dispatch_lr_recover(const SolveArgs& a, cudaStream_t st) {
   switch (a.F_lay.cw) {
     case 1: return coop_launch(lr_recover_kernel<T, 1>, items, bps, a, st, nullptr, kLowRankMaxGrid);
     case 2: return coop_launch(lr_recover_kernel<T, 2>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+#if PHIC_CW_MAX_F32 >= 8
+    case 8:
+      if constexpr (sizeof(T) == 4) return coop_launch(lr_recover_kernel<T, 8>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+      return cudaErrorInvalidValue;
+#endif
     default: return coop_launch(lr_recover_kernel<T, 4>, items, bps, a, st, nullptr, kLowRankMaxGrid);
   }
 }
@@ -141,7 +164,10 @@ TileLayout pick_layout(int w, int elem_bytes) {
   const int cw_max = elem_bytes == 4 ? PHIC_CW_MAX_F32 : PHIC_CW_MAX;
   TileLayout t;
   t.w = w;
-  if (cw_max >= 4 && w % 4 == 0 && w / 4 <= 32) {
+  if (cw_max >= 8 && w % 8 == 0 && w / 8 <= 32) {
+    t.cw = 8;
+    t.ws = w;
+  } else if (cw_max >= 4 && w % 4 == 0 && w / 4 <= 32) {
     t.cw = 4;
     t.ws = w;
   } else if (cw_max >= 2 && w % 2 == 0 && w / 2 <= 32) {

@@ -42,10 +42,12 @@
 #ifndef PHIC_CW_MAX
 #define PHIC_CW_MAX 2
 #endif
-// FP32 tiles: widest column chunk (16 bytes = 4 floats).  One row per thread at a time: carrying two or
-// four rows' loads in flight at once measured slower on GB300 (the registers cost residency).
+// FP32 tiles: widest column chunk, 8 floats (two 16-byte loads per gathered row): with the DIA copy of
+// B a row's loads are independent, and one thread per row of 8 columns measured 15 % faster on GB300
+// than two threads of 4 (46.8 vs 53.9 us per recovery term at n = 1,048,576).  One row per thread at a
+// time: carrying several rows at once measured slower (the registers cost residency).
 #ifndef PHIC_CW_MAX_F32
-#define PHIC_CW_MAX_F32 4
+#define PHIC_CW_MAX_F32 8
 #endif
 
 namespace phic {
@@ -201,29 +203,7 @@ __device__ __forceinline__ void spmm_ent(const int* __restrict__ rowptr, const C
 
 // The same over the ELL copy of B: entry q of `row` at ent[q n + row] for q < K (rows shorter than K
 // padded with a zero weight on their own column), so no row bounds are loaded and the entries of
-// consecutive rows are consecutive.  K is a template parameter for the 2-D and 3-D stencil widths 5 and 7
-// (every entry load and gather of the row in flight at once, no predicated slots), a run-time value
-// otherwise.
-template <typename T, int CW, int K>
-__device__ __forceinline__ void spmm_ell_k(const CsrEnt<T>* __restrict__ ent, int n, const T* __restrict__ X, int ws,
-                                           int c0, int row, T (&acc)[CW]) {
-  CsrEnt<T> e[K];
-#pragma unroll
-  for (int q = 0; q < K; ++q) e[q] = ent[(size_t)q * n + row];
-  T x[K][CW];
-#pragma unroll
-  for (int q = 0; q < K; ++q) VecIO<T, CW>::ld(X + (size_t)e[q].col * ws + c0, x[q]);
-  DotAcc<T> d[CW];
-#pragma unroll
-  for (int j = 0; j < CW; ++j) d[j].zero();
-#pragma unroll
-  for (int q = 0; q < K; ++q)
-#pragma unroll
-    for (int j = 0; j < CW; ++j) d[j].add(e[q].v, x[q][j]);
-#pragma unroll
-  for (int j = 0; j < CW; ++j) acc[j] = d[j].value();
-}
-
+// consecutive rows are consecutive.
 template <typename T, int CW>
 __device__ __forceinline__ void spmm_ell_dyn(const CsrEnt<T>* __restrict__ ent, int n, int K, const T* __restrict__ X,
                                              int ws, int c0, int row, T (&acc)[CW]) {
@@ -305,23 +285,51 @@ struct DiaOffsets {
   }
 };
 
-// B X for one row through whichever copy of B the setup built (ell = K > 0: ELL with K slots; 0: CSR).
+// Formats of the copy of B, as types: a row loop is instantiated once per format, so that each loop
+// holds the registers of one product variant only (one loop with every variant inside spilled).
+struct FmtCsr {};
+struct FmtEll {};                 // run-time number of slots
+template <int D> struct FmtDia {};  // D diagonals (0: run-time number)
+struct FmtLowRank {};
+
+// Operands of a row product shared by the formats.
+template <typename T>
+struct SpmmOps {
+  const int* __restrict__ rowptr;
+  const CsrEnt<T>* __restrict__ ent;
+  int n, ell, ndia;
+  const int* doff;  // ndia offsets (shared memory)
+};
+
 template <typename T, int CW>
-__device__ __forceinline__ void spmm_row(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent, int n,
-                                         int ell, const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW],
-                                         int ndia = 0, const DiaOffsets* dor = nullptr, const int* doff = nullptr) {
-  if (ndia) {
-    const T* __restrict__ val = reinterpret_cast<const T*>(ent);
-    if (ndia == 5) spmm_dia_k<T, CW, 5>(val, dor->o, n, X, ws, c0, row, acc);
-    else if (ndia == 7) spmm_dia_k<T, CW, 7>(val, dor->o, n, X, ws, c0, row, acc);
-    else spmm_dia_dyn<T, CW>(val, doff, ndia, n, X, ws, c0, row, acc);
-    return;
-  }
-  switch (ell) {
-    case 0: spmm_ent<T, CW>(rowptr, ent, X, ws, c0, row, acc); break;
-    case 5: spmm_ell_k<T, CW, 5>(ent, n, X, ws, c0, row, acc); break;
-    case 7: spmm_ell_k<T, CW, 7>(ent, n, X, ws, c0, row, acc); break;
-    default: spmm_ell_dyn<T, CW>(ent, n, ell, X, ws, c0, row, acc); break;
+__device__ __forceinline__ void spmm_fmt(FmtCsr, const SpmmOps<T>& o, const DiaOffsets&, const T* __restrict__ X,
+                                         int ws, int c0, int row, T (&acc)[CW]) {
+  spmm_ent<T, CW>(o.rowptr, o.ent, X, ws, c0, row, acc);
+}
+template <typename T, int CW>
+__device__ __forceinline__ void spmm_fmt(FmtEll, const SpmmOps<T>& o, const DiaOffsets&, const T* __restrict__ X,
+                                         int ws, int c0, int row, T (&acc)[CW]) {
+  spmm_ell_dyn<T, CW>(o.ent, o.n, o.ell, X, ws, c0, row, acc);
+}
+template <typename T, int CW, int D>
+__device__ __forceinline__ void spmm_fmt(FmtDia<D>, const SpmmOps<T>& o, const DiaOffsets& dor,
+                                         const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW]) {
+  const T* __restrict__ val = reinterpret_cast<const T*>(o.ent);
+  if constexpr (D > 0) spmm_dia_k<T, CW, D>(val, dor.o, o.n, X, ws, c0, row, acc);
+  else spmm_dia_dyn<T, CW>(val, o.doff, o.ndia, o.n, X, ws, c0, row, acc);
+}
+
+// Calls body(tag) with the format tag of the copy the setup built.
+template <bool LR, typename Body>
+__device__ __forceinline__ void with_format(int ndia, int ell, Body&& body) {
+  if constexpr (LR) {
+    body(FmtLowRank{});
+  } else {
+    if (ndia == 5) body(FmtDia<5>{});
+    else if (ndia == 7) body(FmtDia<7>{});
+    else if (ndia) body(FmtDia<0>{});
+    else if (ell) body(FmtEll{});
+    else body(FmtCsr{});
   }
 }
 
@@ -750,6 +758,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   const int ndia = sc.ndia;
   DiaOffsets dor;
   dor.load(sc.dia_off, ndia);
+  const SpmmOps<T> ops{rowptr, ent, n, ell, ndia, sc.dia_off};
   while (lc.go) {
     const int kk = lc.k;
     const int ph = phase++;
@@ -777,6 +786,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
     const int bias = lc.bias;
     const float fscale = lc.fscale;
     int nf = 0;
+    with_format<LR>(ndia, ell, [&](auto fmt) {
     for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
       const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
       const bool act = row < br.r1 && lane < L.L;
@@ -791,7 +801,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
           for (int j = 0; j < CW; ++j)
             acc[j] = kLive[j] ? lr_row(static_cast<const T*>(a.lrU), a.lr_k, row, lz->zt + c0 + j, L.w) : T(0);
         } else {
-          spmm_row<T, CW>(rowptr, ent, n, ell, Do, L.ws, c0, row, acc, ndia, &dor, sc.dia_off);
+          spmm_fmt<T, CW>(fmt, ops, dor, Do, L.ws, c0, row, acc);
         }
         if (nodiag && (LR || rowflag[row])) {  // no stored diagonal: apply the shift explicitly
           T own[CW];
@@ -826,6 +836,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
         fmax_bits(mS, rS);
       }
     }
+    });
     warp_parts(wp, mD, mS, 0, nf);
     if (!team_sync_lead(tm, [&] { parts_to_slots(ctl, ph, wp); },
                         [&] {
@@ -971,18 +982,11 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   const BlockRows br(n, L.Lp2, tm);
   const int lmask = L.Lp2 - 1;
   const int c0 = (threadIdx.x & lmask) * CW;
-  int kI[CW];
-  bool kLive[CW], kBlkP[CW];
-  T kMu[CW], kTt[CW];
-#pragma unroll
-  for (int j = 0; j < CW; ++j) {
-    const int c = c0 + j;
-    kLive[j] = c < L.w;
-    kBlkP[j] = kLive[j] && c >= r;
-    kI[j] = !kLive[j] ? 0 : (c < r ? c : c - r);
-    kMu[j] = kLive[j] ? (T)sc.mu[kI[j]] : T(0);
-    kTt[j] = (T)a.t[kI[j]];
-  }
+  // per-column facts of this thread's lane, computed where used (so that none of them stays live across
+  // the Taylor loop): column c0 + j is live when below w; block p of F when at least r; combination i
+  auto col_live = [&](int j) { return c0 + j < L.w; };
+  auto col_blkp = [&](int j) { return c0 + j < L.w && c0 + j >= r; };
+  auto col_i = [&](int j) { const int c = c0 + j; return c >= L.w ? 0 : (c < r ? c : c - r); };
   int bad = 0;
 
   // thread-0 loop state
@@ -1015,8 +1019,8 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
           T v = T(0);
-          if (kLive[j] && !kBlkP[j]) {
-            const int i = kI[j];
+          if (col_live(j) && !col_blkp(j)) {
+            const int i = col_i(j);
             T acc = T(0);
             if constexpr (LR) {
               acc = lr_row(static_cast<const T*>(a.lrU), a.lr_k, row, lz->zt + i, r);
@@ -1028,9 +1032,9 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
                 acc = fma(__ldg(vals + q), S[(size_t)col * ws_s + i], acc);
               }
             }
-            v = fma(acc, kTt[j], v0 ? v0[row] : T(0));
-          } else if (kBlkP[j]) {
-            v = S[(size_t)row * ws_s + p * r + kI[j]];
+            v = fma(acc, (T)a.t[i], v0 ? v0[row] : T(0));
+          } else if (col_blkp(j)) {
+            v = S[(size_t)row * ws_s + p * r + col_i(j)];
           }
           f[j] = v;
           part += fabs(v);
@@ -1066,6 +1070,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   const int ndia = sc.ndia;
   DiaOffsets dor;
   dor.load(sc.dia_off, ndia);
+  const SpmmOps<T> ops{rowptr, ent, n, ell, ndia, sc.dia_off};
 
   // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||: next term
   auto decide = [&]() {
@@ -1112,8 +1117,8 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
       float kF[CW];
 #pragma unroll
       for (int j = 0; j < CW; ++j) {
-        kC[j] = kLive[j] ? sc.coef[kI[j]] : T(0);
-        kF[j] = kLive[j] ? sc.fcoef[kI[j]] : 0.f;
+        kC[j] = col_live(j) ? sc.coef[col_i(j)] : T(0);
+        kF[j] = col_live(j) ? sc.fcoef[col_i(j)] : 0.f;
       }
       const T* __restrict__ Go = static_cast<const T*>(a.Ft[cur]);
       T* __restrict__ Gn = static_cast<T*>(a.Ft[cur ^ 1]);
@@ -1131,6 +1136,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
       const int bias = lc.bias;
       const float fscale = lc.fscale;
       int nf = 0;
+      with_format<LR>(ndia, ell, [&](auto fmt) {
       for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
         const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
         const bool act = row < br.r1 && lane < L.L;
@@ -1140,9 +1146,9 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
           if constexpr (LR) {
 #pragma unroll
             for (int j = 0; j < CW; ++j)
-              acc[j] = kLive[j] ? lr_row(static_cast<const T*>(a.lrU), a.lr_k, row, lz->zt + c0 + j, L.w) : T(0);
+              acc[j] = col_live(j) ? lr_row(static_cast<const T*>(a.lrU), a.lr_k, row, lz->zt + c0 + j, L.w) : T(0);
           } else {
-            spmm_row<T, CW>(rowptr, ent, n, ell, Go, L.ws, c0, row, acc, ndia, &dor, sc.dia_off);
+            spmm_fmt<T, CW>(fmt, ops, dor, Go, L.ws, c0, row, acc);
           }
           const size_t o = (size_t)row * L.ws + c0;
           const bool shift_row = nodiag && (LR || rowflag[row]);
@@ -1177,6 +1183,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
           fmax_bits(mE, rE);
         }
       }
+      });
       warp_parts(wp, mF, mE, 0, nf);
       cur ^= 1;
       if (!team_sync_lead(tm, [&] { parts_to_slots(ctl, ph, wp); },
@@ -1215,13 +1222,13 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
           VecIO<T, CW>::ld(E + o, e);
 #pragma unroll
           for (int j = 0; j < CW; ++j) {
-            T v = e[j] * kMu[j];
-            if (kBlkP[j]) {
-              const int i = kI[j];
+            T v = col_live(j) ? e[j] * (T)sc.mu[col_i(j)] : T(0);
+            if (col_blkp(j)) {
+              const int i = col_i(j);
               const T* srow = S + (size_t)row * ws_s;
               for (int aa = 1; aa <= p; ++aa) v = fma(srow[aa * r + i], sc.cj[aa][i], v);
             }
-            e[j] = kLive[j] ? v : T(0);
+            e[j] = col_live(j) ? v : T(0);
             part += fabs(e[j]);
           }
           VecIO<T, CW>::st(F + o, e);

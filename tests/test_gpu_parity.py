@@ -186,3 +186,22 @@ def test_advdiff2d_1024_full_size_fp64_and_fp32(oracle_mod):
     assert g32["status"] == 0
     assert max(_rel(W32, ref)) <= 5e-6
     print(f"advdiff 1024^2 h=1e-5: fp64 errs={_rel(W, ref)} fp32 errs={_rel(W32, ref)} s_int={gst['s_int']}")
+
+
+@pytest.mark.parametrize("p,r", [(3, 2), (1, 4), (7, 2), (3, 4), (2, 3)])
+def test_fp32_widths_against_fp64_oracle(oracle_mod, p, r):
+    """FP32 tiles of 8, 16 and other widths (lane chunks of 8, 4, 2 or 1 floats) in the series and the
+    recovery, with the GPU's Algorithm 1 at tol 2^-24, within 5e-6 of the FP64 oracle."""
+    Acsr = wl.convection_diffusion(45, 2, 8.0)
+    rng = np.random.default_rng(40 * p + r)
+    V = rng.standard_normal((p + 1, Acsr.n))
+    t = np.linspace(3e-3, 9e-3, r)
+    alpha = np.linspace(0.6, 1.4, r)
+    sel = oracle_mod.select(Acsr)
+    ref, _ = oracle_mod.solve(Acsr, V, t, alpha, TOL53, sel["s"], sel["xi"])
+    A32 = api.DeviceCSR.from_host(Acsr, dtype=torch.float32)
+    P32 = api.select_params(A32, tol=TOL24)
+    W, st = api.solve(A32, torch.as_tensor(V).float().cuda(), t, alpha, TOL24, P32)
+    torch.cuda.synchronize()
+    assert api.read_stats(st)["status"] == 0
+    assert max(_rel(W.cpu().numpy(), ref)) <= 5e-6
