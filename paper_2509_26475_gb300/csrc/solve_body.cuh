@@ -171,27 +171,33 @@ struct DotAcc<float> {
 };
 #endif
 
-// acc[j] = sum_q B(row, col_q) X(col_q, c0 + j) over the row's stored entries, four at a time so that
-// their gathers are in flight together.  Columns were checked when the entries were written.
+// Entries gathered together by the CSR and ELL products: four, or two when a lane's chunk of a row is
+// 32 bytes (four such gathers spilled at 80 registers a thread).
+template <typename T, int CW>
+constexpr int kGatherBatch = CW * sizeof(T) >= 32 ? 2 : 4;
+
+// acc[j] = sum_q B(row, col_q) X(col_q, c0 + j) over the row's stored entries, kGatherBatch at a time so
+// that their gathers are in flight together.  Columns were checked when the entries were written.
 template <typename T, int CW>
 __device__ __forceinline__ void spmm_ent(const int* __restrict__ rowptr, const CsrEnt<T>* __restrict__ ent,
                                          const T* __restrict__ X, int ws, int c0, int row, T (&acc)[CW]) {
+  constexpr int U = kGatherBatch<T, CW>;
   const int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
   DotAcc<T> d[CW];
 #pragma unroll
   for (int j = 0; j < CW; ++j) d[j].zero();
-  for (int q0 = beg; q0 < end; q0 += 4) {
+  for (int q0 = beg; q0 < end; q0 += U) {
     const int cnt = end - q0;
-    CsrEnt<T> e[4];
+    CsrEnt<T> e[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < U; ++u)
       if (u < cnt) e[u] = ent[q0 + u];
-    T x[4][CW];
+    T x[U][CW];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < U; ++u)
       if (u < cnt) VecIO<T, CW>::ld(X + (size_t)e[u].col * ws + c0, x[u]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < U; ++u)
       if (u < cnt) {
 #pragma unroll
         for (int j = 0; j < CW; ++j) d[j].add(e[u].v, x[u][j]);
@@ -207,20 +213,21 @@ __device__ __forceinline__ void spmm_ent(const int* __restrict__ rowptr, const C
 template <typename T, int CW>
 __device__ __forceinline__ void spmm_ell_dyn(const CsrEnt<T>* __restrict__ ent, int n, int K, const T* __restrict__ X,
                                              int ws, int c0, int row, T (&acc)[CW]) {
+  constexpr int U = kGatherBatch<T, CW>;
   DotAcc<T> d[CW];
 #pragma unroll
   for (int j = 0; j < CW; ++j) d[j].zero();
-  for (int q0 = 0; q0 < K; q0 += 4) {
-    CsrEnt<T> e[4];
+  for (int q0 = 0; q0 < K; q0 += U) {
+    CsrEnt<T> e[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < U; ++u)
       if (q0 + u < K) e[u] = ent[(size_t)(q0 + u) * n + row];
-    T x[4][CW];
+    T x[U][CW];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < U; ++u)
       if (q0 + u < K) VecIO<T, CW>::ld(X + (size_t)e[u].col * ws + c0, x[u]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < U; ++u)
       if (q0 + u < K) {
 #pragma unroll
         for (int j = 0; j < CW; ++j) d[j].add(e[u].v, x[u][j]);
@@ -333,6 +340,26 @@ __device__ __forceinline__ void with_format(int ndia, int ell, Body&& body) {
   }
 }
 
+// Where the switch on the format goes.  A Taylor loop nest runs under loop_format; each row loop in it
+// runs under row_format.  With kSplit the switch encloses the whole nest, which is then instantiated
+// once per format and gets a register allocation of its own (with one nest for all formats, the widest
+// format's needs made the 5-diagonal loop spill its loop state: 47 against 36 us per FP32 recovery term
+// at n = 1,048,576 on GB300).  Without it (kernels that run many small problems, where code size and
+// build time matter more) one nest switches at every row loop: its tag is FmtAny.
+struct FmtAny {};
+template <typename F> constexpr bool kIsFmtAny = false;
+template <> constexpr bool kIsFmtAny<FmtAny> = true;
+template <bool kSplit, bool LR, typename Body>
+__device__ __forceinline__ void loop_format(int ndia, int ell, Body&& body) {
+  if constexpr (kSplit) with_format<LR>(ndia, ell, body);
+  else body(FmtAny{});
+}
+template <bool LR, typename Fmt, typename Body>
+__device__ __forceinline__ void row_format(Fmt f, int ndia, int ell, Body&& body) {
+  if constexpr (kIsFmtAny<Fmt>) with_format<LR>(ndia, ell, body);
+  else body(f);
+}
+
 // |x| 2^-e0 as an FP32 value, for the infinity-norm sums that feed the truncation test.  For a double
 // the high word (sign, exponent, 20 mantissa bits) is rebiased into FP32 layout with integer
 // operations (relative truncation below 2^-20; values under 2^-126 of the scale flush to 0, values above
@@ -433,7 +460,7 @@ struct LowRankSmem {
 //
 // Runs on the team tm; `phase` is the team's next slot phase (advanced by one per barrier).  Thread 0
 // of rank 0 records the outcome in a.state (status, s_int, term count, xi, s, eA, nodiag) on every exit.
-template <typename T, int CW, bool LR = false>
+template <typename T, int CW, bool LR = false, bool kSplit = false>
 __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSmem<T>& sm, int& phase,
                                           LowRankSmem<T>* lz = nullptr) {
   SeriesScalars& sc = sm.sc;
@@ -759,6 +786,10 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   DiaOffsets dor;
   dor.load(sc.dia_off, ndia);
   const SpmmOps<T> ops{rowptr, ent, n, ell, ndia, sc.dia_off};
+  // the term loop per format of B (kSplit) or one loop for all (see loop_format); a barrier that times
+  // out ends it with out = PHIC_TIMEOUT
+  int out = PHIC_OK;
+  loop_format<kSplit, LR>(ndia, ell, [&](auto lfmt) {
   while (lc.go) {
     const int kk = lc.k;
     const int ph = phase++;
@@ -776,8 +807,10 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
     T* __restrict__ Dn = static_cast<T*>(a.Dt[kk & 1]);
     if constexpr (LR) {  // Z = W^T D 2^-eA for this term's products
       if (!lr_reduce(tm, static_cast<const T*>(a.lrW), a.lr_k, L.w, br.r0, br.r1,
-                     [&](int row, int c) { return (double)Do[(size_t)row * L.ws + c]; }, a.lr_part, lz->zs))
-        return PHIC_TIMEOUT;
+                     [&](int row, int c) { return (double)Do[(size_t)row * L.ws + c]; }, a.lr_part, lz->zs)) {
+        out = PHIC_TIMEOUT;
+        return;
+      }
       const double scaleB = ldexp(1.0, -sc.eA);
       for (int e = threadIdx.x; e < a.lr_k * L.w; e += kBlock) lz->zt[e] = (T)(lz->zs[e] * scaleB);
       __syncthreads();
@@ -786,7 +819,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
     const int bias = lc.bias;
     const float fscale = lc.fscale;
     int nf = 0;
-    with_format<LR>(ndia, ell, [&](auto fmt) {
+    row_format<LR>(lfmt, ndia, ell, [&](auto fmt) {
     for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
       const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
       const bool act = row < br.r1 && lane < L.L;
@@ -845,16 +878,19 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
                           c2 = slot_norm(ctl, ph, 0, e0);  // ||D_k||_inf / k!
                           nS = slot_norm(ctl, ph, 1, e0);
                           decide();
-                        }))
-      return PHIC_TIMEOUT;
+                        })) {
+      out = PHIC_TIMEOUT;
+      return;
+    }
   }
-  return lc.status;
+  });
+  return out != PHIC_OK ? out : lc.status;
 }
 
-template <typename T, int CW, bool LR = false>
+template <typename T, int CW, bool LR = false, bool kSplit = false>
 __device__ __forceinline__ void series_body(const SolveArgs& a, Team& tm, SeriesSmem<T>& sm, int& phase,
                                             LowRankSmem<T>* lz = nullptr) {
-  int st = series_run<T, CW, LR>(a, tm, sm, phase, lz);
+  int st = series_run<T, CW, LR, kSplit>(a, tm, sm, phase, lz);
   if (tm.rank == 0 && threadIdx.x == 0) {
     if (st != PHIC_OK) set_status(tm.ctl, st);
     SolveState* sv = a.state;
@@ -902,7 +938,7 @@ __device__ __forceinline__ void jt_power_coeffs(RecoverScalars<T>& rs, const Sol
 // max_steps outer steps j; it writes the output once j reaches s_int - 1, and otherwise records in
 // a.state where the next slice resumes.  Returns 1 once the solve is finished (output written or an
 // error recorded).
-template <typename T, int CW, bool LR = false>
+template <typename T, int CW, bool LR = false, bool kSplit = false>
 __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, RecoverSmem<T>& sm, int& phase,
                                             int max_steps, LowRankSmem<T>* lz = nullptr) {
   RecoverScalars<T>& sc = sm.sc;
@@ -1098,6 +1134,10 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   const int j_first = sc.j_done + 1;
   const long long j_stop = (long long)sc.j_done + (long long)max_steps;
   int jstep = j_first;
+  // the loop over j per format of B (kSplit) or one loop for all (see loop_format); a barrier that times
+  // out ends it with timed_out
+  bool timed_out = false;
+  loop_format<kSplit, LR>(ndia, ell, [&](auto lfmt) {
   for (; jstep <= sc.s_int - 1 && jstep <= j_stop && lc.status == PHIC_OK; ++jstep) {
     if (threadIdx.x == 0) {
       k = 0;
@@ -1125,8 +1165,8 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
       if constexpr (LR) {  // Z = W^T G 2^-eA for this term's products
         if (!lr_reduce(tm, static_cast<const T*>(a.lrW), a.lr_k, L.w, br.r0, br.r1,
                        [&](int row, int c) { return (double)Go[(size_t)row * L.ws + c]; }, a.lr_part, lz->zs)) {
-          finish(PHIC_TIMEOUT);
-          return 1;
+          timed_out = true;
+          return;
         }
         const double scaleB = ldexp(1.0, -sc.eA);
         for (int e = threadIdx.x; e < a.lr_k * L.w; e += kBlock) lz->zt[e] = (T)(lz->zs[e] * scaleB);
@@ -1136,7 +1176,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
       const int bias = lc.bias;
       const float fscale = lc.fscale;
       int nf = 0;
-      with_format<LR>(ndia, ell, [&](auto fmt) {
+      row_format<LR>(lfmt, ndia, ell, [&](auto fmt) {
       for (long long it = threadIdx.x; it < br.padded; it += kBlock) {
         const int row = br.r0 + (int)(it >> br.shift), lane = (int)(it & lmask);
         const bool act = row < br.r1 && lane < L.L;
@@ -1194,8 +1234,8 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
                             nE = slot_norm(ctl, ph, 1, e0);
                             decide();
                           })) {
-        finish(PHIC_TIMEOUT);
-        return 1;
+        timed_out = true;
+        return;
       }
     }
     if (leader) {
@@ -1243,10 +1283,15 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
                             status = read_status(ctl);
                             lc.status = status;
                           })) {
-        finish(PHIC_TIMEOUT);
-        return 1;
+        timed_out = true;
+        return;
       }
     }
+  }
+  });
+  if (timed_out) {
+    finish(PHIC_TIMEOUT);
+    return 1;
   }
 
   if (lc.status == PHIC_OK && jstep <= sc.s_int - 1) {
