@@ -125,9 +125,9 @@ def torch_dtype():
 
 def recorded_traffic(terms: int):
     """DRAM bytes of one launch of the dominant kernel from the committed ncu record of this workload and
-    precision, if that record was taken on the current kernel source (sha256); None otherwise.  A record
-    of a shorter launch of the same kernel (fewer Taylor terms) is scaled by the terms: every term moves
-    the same bytes once the working set exceeds L2, which is when the scaling is used."""
+    precision, if that record was taken on the current kernel sources (sha256 of each); None otherwise.
+    A record of a shorter launch of the same kernel (fewer Taylor terms) is scaled by the terms: every
+    term moves the same bytes once the working set exceeds L2, which is when the scaling is used."""
     import hashlib
 
     name = "recover_kernel_convdiff3d_64.json" if (WORKLOAD, PRECISION) == ("convdiff3d-64", "f64") else \
@@ -136,9 +136,9 @@ def recorded_traffic(terms: int):
         return None
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", name)))
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() != rec["sha256"]:
-            return None
+        for path, sha in rec["sources"].items():  # every file that defines the kernel, as captured
+            if hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest() != sha:
+                return None
         b = float(rec["dram_bytes_per_launch"])
         if "terms_per_launch" in rec:
             b *= terms / float(rec["terms_per_launch"])
