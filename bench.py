@@ -30,8 +30,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "φ-comb solves/s & SpMM HBM GB/s (% peak) at stated tol; p50/p99 serve latency"
-# FP64 pipe of a GB300 SM: 2 FMA/clk (1.91 measured), 152 SMs, 2070 MHz maximum SM clock.
-FP64_PEAK_GOPS = 2.0 * 152 * 2.070
+# FP64 pipe of a GB300 SM: 2 FMA/clk (1.91 measured), 152 SMs, 2070 MHz maximum SM clock; 2 flops an FMA.
+FP64_PEAK_GFLOPS = 2.0 * 2.0 * 152 * 2.070
 
 # Workload of the benchmark line (defaults) and the auxiliary FP32/FP64 precision workload.
 WORKLOADS = {
@@ -267,17 +267,16 @@ class ClockSampler:
 # Native run
 # ------------------------------------------------------------------------------------------------
 def recover_kernel_work(n, nnz, wf, p, r, terms, outer_steps, b=8):
-    """Algorithmic FP64 operations and bytes of one recovery-kernel launch.
+    """Algorithmic FP64 flops (an FMA counts 2) and bytes of one recovery-kernel launch.
 
-    Per Taylor term (n x wf block, wf = 2r): the product with A_1 = A - xi I (formed once per solve, as
-    Algorithm 3 writes it) takes nnz multiply-adds per column, the column scale t_i/(s k) n,
-    E <- E + F n, and the two infinity-norm row sums 2n operations per column: (nnz + 4n) wf.  Per
-    recovery step the refresh E mu + S Jt costs (2 + p/2) n wf.  Bytes per term: CSR values and indices
-    ((4 + b) nnz + 4(n+1)) plus reading F, reading and writing E and writing the next F (4 n wf b), with b
-    the bytes of a value (8 in FP64, 4 in FP32)."""
-    ops = terms * (nnz + 4 * n) * wf + outer_steps * (2 + p / 2.0) * n * wf
+    Per Taylor term (n x wf block, wf = 2r): the product with A_1 = A - xi I takes 2 nnz flops per
+    column, and the column scale, the accumulation E <- E + F and the norm about 3 n more:
+    (2 nnz + 3 n) wf.  Per recovery step the refresh E mu + S Jt costs about (1 + p) n wf.  Bytes per term:
+    CSR values and indices ((4 + b) nnz + 4(n+1)) plus reading F, reading and writing E and writing the
+    next F (4 n wf b), with b the bytes of a value (8 in FP64, 4 in FP32)."""
+    flops = terms * (2 * nnz + 3 * n) * wf + outer_steps * (1 + p) * n * wf
     bytes_ = terms * ((4 + b) * nnz + 4 * (n + 1) + 4 * n * wf * b)
-    return ops, bytes_
+    return flops, bytes_
 
 
 def main():
@@ -375,9 +374,9 @@ def main():
     prm = api.read_params(params)
     wf = 2 * R
     b = 8 if PRECISION == "f64" else 4
-    ops, bytes_ = recover_kernel_work(n, nnz, wf, P, R, st_last["recovery_terms"], st_last["s_int"] - 1, b)
+    flops, bytes_ = recover_kernel_work(n, nnz, wf, P, R, st_last["recovery_terms"], st_last["s_int"] - 1, b)
     rec_s = statistics.mean(rec_ms) / 1000.0
-    achieved = ops / rec_s / 1e9
+    achieved = flops / rec_s / 1e9
     hbm_gbs = bytes_ / rec_s / 1e9
     peaks = {}
     try:
@@ -388,10 +387,11 @@ def main():
     kernel = f"recover_kernel (Algorithm 3 recovery loop, h={HS[-1]:g})"
     if PRECISION == "f64":
         roofline = {"bound": "alu", "kernel": kernel,
-                    "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
-                    "frac": achieved / FP64_PEAK_GOPS,
+                    "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "FP64 GFLOP/s",
+                    "frac": achieved / FP64_PEAK_GFLOPS,
                     "traffic": recorded_traffic(st_last["recovery_terms"]),
-                    "peak_note": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (probe measured 1.91 FMA/clk/SM)",
+                    "peak_note": "FP64 pipe: 2 FMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (probe measured "
+                                 "1.91 FMA/clk/SM); achieved counts (2 nnz + 3 n) 2r flops per Taylor term",
                     "launch_ms": statistics.mean(rec_ms), "terms_per_launch": st_last["recovery_terms"],
                     "hbm_view": {"algorithmic_gbs": hbm_gbs, "peak_gbs": hbm_peak,
                                  "frac_of_measured": hbm_gbs / hbm_peak}}
@@ -766,6 +766,12 @@ def run_serve(args, rank, world, local_rank):
     hbm_peak = float(_peaks().get("hbm_gbs", 6800.0))
     achieved = nbytes / busy_s / 1e9 if busy_s > 0 else 0.0
     value = len(infos) / span
+    # bytes the server copies per request: the operator's CSR arrays (none for a registered operator)
+    # and V in, W out
+    def _nb(x):
+        return 0 if x is None else x.numel() * x.element_size()
+    h2d = int(sum(_nb(q.rowptr) + _nb(q.colidx) + _nb(q.values) + _nb(q.V) for q in hostreq))
+    d2h = int(sum(_nb(q.W) for q in hostreq))
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
             "ms_per_step": span * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32", "data": "synthetic",
@@ -786,8 +792,9 @@ def run_serve(args, rank, world, local_rank):
                          "traffic": None, "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured); "
                                                        "algorithmic bytes over the slices' device time"},
             "gpu_launches": int(c1["slices"] - c0["slices"]) * 2, "wall_s_timed_region": t_end - t_start,
-            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
-                    "note": "the serving numbers are end to end already: host inputs in, results on the host"}}
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "note": "the serving numbers are end to end already: host inputs in, results on the host; "
+                            "the step is the whole stream"}}
     clk_sum = clk.summary()
     if clk_sum:
         line["clocks"] = clk_sum

@@ -99,7 +99,17 @@ typedef struct {
   int64_t spmm_count;      /* sparse block products performed */
   double xi;               /* shift used */
   double s;                /* scaling parameter used */
+  int32_t op_format;       /* copy of B = (A - xi I) 2^-eA the products read: PHIC_OP_* */
+  int32_t op_slots;        /* its diagonals (DIA) or entries per row (ELL); 0 otherwise */
 } phic_stats;
+
+/* phic_stats.op_format.  The setup picks DIA (the values of at most 16 diagonals, row-aligned) when
+ * the stored diagonals are that few and fill the rows well, else ELL (a fixed number of slots per row,
+ * at most 64) when n times the longest row fits the copy's room, else the entries in CSR order. */
+#define PHIC_OP_CSR 0
+#define PHIC_OP_ELL 1
+#define PHIC_OP_DIA 2
+#define PHIC_OP_LOWRANK 3
 
 /* Flags of phic_solve */
 #define PHIC_NO_V0 1u /* V holds v_1..v_p only (p rows); the result is sum_{j>=1} alpha_i^j phi_j(t_i A) v_j
@@ -470,6 +480,13 @@ uint64_t phic_launch_count(void);
 
 /* Library version as 10000*major + 100*minor + patch. */
 int32_t phic_version(void);
+
+/* Sizes in bytes of the public structs, so that a binding can check its layouts: out[i] for i < n (in
+ * this order: phic_csr, phic_select_opts, phic_params, phic_stats, phic_lowrank, phic_batch_item,
+ * phic_batch_config, phic_batch_info, phic_server_config, phic_operator, phic_request,
+ * phic_request_info, phic_server_counters).  Returns how many there are (13), whatever n is; out may be
+ * NULL when n is 0. */
+int32_t phic_struct_sizes(size_t* out, int32_t n);
 
 #ifdef __cplusplus
 }

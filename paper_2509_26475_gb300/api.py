@@ -126,7 +126,9 @@ def read_stats(stats: torch.Tensor) -> dict:
     raw = stats.detach().cpu().numpy().tobytes()
     s = capi.phic_stats.from_buffer_copy(raw)
     return dict(status=s.status, s_int=s.s_int, series_terms=s.series_terms, max_inner_terms=s.max_inner_terms,
-                recovery_terms=s.recovery_terms, spmm_count=s.spmm_count, xi=s.xi, s=s.s)
+                recovery_terms=s.recovery_terms, spmm_count=s.spmm_count, xi=s.xi, s=s.s,
+                op_format=("csr", "ell", "dia", "lowrank")[s.op_format] if 0 <= s.op_format <= 3 else s.op_format,
+                op_slots=s.op_slots)
 
 
 def select_params(A: DeviceCSR, m: int = 61, tol: float = 2.0**-53, delta: float = 0.8, seed: int = 0x5EED,

@@ -49,7 +49,8 @@ class phic_params(ctypes.Structure):
 class phic_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("s_int", ctypes.c_int32), ("series_terms", ctypes.c_int32),
                 ("max_inner_terms", ctypes.c_int32), ("recovery_terms", ctypes.c_int64),
-                ("spmm_count", ctypes.c_int64), ("xi", ctypes.c_double), ("s", ctypes.c_double)]
+                ("spmm_count", ctypes.c_int64), ("xi", ctypes.c_double), ("s", ctypes.c_double),
+                ("op_format", ctypes.c_int32), ("op_slots", ctypes.c_int32)]
 
 
 class phic_lowrank(ctypes.Structure):
@@ -107,6 +108,10 @@ class phic_server_counters(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("slices", ctypes.c_int64), ("max_slice_requests", ctypes.c_int64),
                 ("arena_in_use", ctypes.c_int64), ("arena_peak", ctypes.c_int64), ("gpu_busy_ms", ctypes.c_double)]
+
+# The public structs in the order phic_struct_sizes reports them.
+STRUCTS = (phic_csr, phic_select_opts, phic_params, phic_stats, phic_lowrank, phic_batch_item, phic_batch_config,
+           phic_batch_info, phic_server_config, phic_operator, phic_request, phic_request_info, phic_server_counters)
 
 
 PHIC_REQ_QUEUED, PHIC_REQ_LOADING, PHIC_REQ_RUNNING, PHIC_REQ_COPYING, PHIC_REQ_DONE = range(5)
@@ -173,6 +178,7 @@ SIGNATURES = [
     ("phic_status_string", ctypes.c_char_p, [ctypes.c_int32]),
     ("phic_launch_count", ctypes.c_uint64, []),
     ("phic_version", ctypes.c_int32, []),
+    ("phic_struct_sizes", ctypes.c_int32, [ctypes.POINTER(ctypes.c_size_t), ctypes.c_int32]),
 ]
 
 

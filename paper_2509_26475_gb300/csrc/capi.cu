@@ -130,7 +130,18 @@ const char* phic_status_string(int32_t s) {
 
 uint64_t phic_launch_count(void) { return g_launches.load(); }
 
-int32_t phic_version(void) { return 100; }
+int32_t phic_version(void) { return 101; }
+
+int32_t phic_struct_sizes(size_t* out, int32_t n) {
+  const size_t sizes[] = {sizeof(phic_csr),           sizeof(phic_select_opts),  sizeof(phic_params),
+                          sizeof(phic_stats),         sizeof(phic_lowrank),      sizeof(phic_batch_item),
+                          sizeof(phic_batch_config),  sizeof(phic_batch_info),   sizeof(phic_server_config),
+                          sizeof(phic_operator),      sizeof(phic_request),      sizeof(phic_request_info),
+                          sizeof(phic_server_counters)};
+  const int32_t count = (int32_t)(sizeof(sizes) / sizeof(sizes[0]));
+  for (int32_t i = 0; out && i < n && i < count; ++i) out[i] = sizes[i];
+  return count;
+}
 
 }  // extern "C"
 

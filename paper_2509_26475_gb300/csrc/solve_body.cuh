@@ -1002,6 +1002,8 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
         a.stats->spmm_count = (long long)(sc.series_terms - 1) + 1 + rec_terms;
         a.stats->xi = sc.xi;
         a.stats->s = vs->s;
+        a.stats->op_format = LR ? PHIC_OP_LOWRANK : sc.ndia ? PHIC_OP_DIA : sc.ell ? PHIC_OP_ELL : PHIC_OP_CSR;
+        a.stats->op_slots = LR ? 0 : sc.ndia ? sc.ndia : sc.ell;
       }
     }
   };

@@ -108,6 +108,31 @@ def _grid_operator(shape, coeff_center, coeff_minus, coeff_plus) -> CSR:
     return CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), vals.astype(np.float64))
 
 
+def graph_operator(n: int, degree: int, seed: int, hubs: int = 0, hub_degree: int = 0) -> CSR:
+    """A = -(L + I) for the weighted Laplacian L = D - W of a random graph on n nodes: degree // 2
+    random permutations join i to perm(i), and `hubs` nodes are joined to hub_degree random nodes each;
+    weights U(0.5, 1.5), symmetric.  A is symmetric negative definite (eigenvalues in [-1 - 2 max
+    weighted degree, -1]); its rows are near-uniform in length (degree + 1) except at the hubs, and its
+    stored diagonals are scattered."""
+    import scipy.sparse as sp
+
+    rng = np.random.default_rng(seed)
+    src, dst = [], []
+    for _ in range(degree // 2):
+        src.append(np.arange(n)); dst.append(rng.permutation(n))
+    for h in rng.choice(n, size=hubs, replace=False) if hubs else []:
+        src.append(np.full(hub_degree, h)); dst.append(rng.choice(n, size=hub_degree, replace=False))
+    src = np.concatenate(src) if src else np.zeros(0, dtype=np.int64)
+    dst = np.concatenate(dst) if dst else np.zeros(0, dtype=np.int64)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    w = rng.uniform(0.5, 1.5, size=src.size)
+    Wm = sp.coo_matrix((w, (src, dst)), shape=(n, n)).tocsr()
+    Wm = Wm + Wm.T
+    L = sp.diags(np.asarray(Wm.sum(axis=1)).ravel()) - Wm
+    return from_scipy(-(L + sp.identity(n)))
+
+
 def laplacian_2d(nx: int, ny: int | None = None) -> CSR:
     ny = nx if ny is None else ny
     h = 1.0 / (nx + 1)

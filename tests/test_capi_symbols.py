@@ -46,3 +46,18 @@ def test_host_queries_without_gpu():
     assert lib.phic_solve_workspace_size(10, 50, 16, 1, 0, ctypes.byref(out)) == capi.PHIC_INVALID_ARG
     assert lib.phic_select_workspace_size(1000, 61, ctypes.byref(out)) == 0
     assert out.value >= 1000 * 62 * 8
+
+
+def test_binding_struct_layouts_match_the_library():
+    """Every public struct has the same size in the ctypes binding as in the compiled library."""
+    import ctypes
+
+    from paper_2509_26475_gb300 import capi
+
+    lib = capi.load(build_if_missing=True)
+    count = lib.phic_struct_sizes(None, 0)
+    assert count == len(capi.STRUCTS)
+    sizes = (ctypes.c_size_t * count)()
+    assert lib.phic_struct_sizes(sizes, count) == count
+    for cls, size in zip(capi.STRUCTS, sizes):
+        assert ctypes.sizeof(cls) == size, (cls.__name__, ctypes.sizeof(cls), size)
