@@ -71,7 +71,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="convdiff3d-64", choices=sorted(WORKLOADS) + ["batch512", "serve"])
+    ap.add_argument("--workload", default="convdiff3d-64",
+                    choices=sorted(WORKLOADS) + ["batch512", "serve", "exprk-adr", "lowrank-m2"])
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "mixed"])
     ap.add_argument("--requests", type=int, default=1000, help="serve: number of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate (requests/s)")
@@ -194,6 +195,12 @@ def run_reference(args, rank, world):
         return 0
     if WORKLOAD in ("batch512", "serve"):
         return run_reference_fleet(args)
+    if WORKLOAD == "exprk-adr":
+        return run_reference_exprk(args)
+    if WORKLOAD == "lowrank-m2":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle takes dense or CSR operators; the dense "
+                          "form of the 400,000-row low-rank operator (1.3 TB) does not fit"}), flush=True)
+        return 0
     steps, warmup = max(1, args.steps), max(0, args.warmup)
     # bound the whole run to a few minutes: at most 6 timed steps and 1 warm-up of the full oracle step
     steps_run, warm_run = min(steps, 6), min(warmup, 1)
@@ -291,6 +298,10 @@ def main():
         return run_batch(args, rank, world, local_rank)
     if WORKLOAD == "serve":
         return run_serve(args, rank, world, local_rank)
+    if WORKLOAD == "exprk-adr":
+        return run_exprk(args, rank, world, local_rank)
+    if WORKLOAD == "lowrank-m2":
+        return run_lowrank(args, rank, world, local_rank)
     import numpy as np
     import torch
 
@@ -800,6 +811,236 @@ def run_serve(args, rank, world, local_rank):
         line["clocks"] = clk_sum
     srv.close()
     print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# The expRK4s6 driver on the ADR problem (exprk-adr) and a low-rank operator (lowrank-m2)
+# ------------------------------------------------------------------------------------------------
+# One bounded team barrier at 304 blocks on GB300 (microbenchmark): the floor of a Taylor term whose
+# working set is L2-resident.
+BARRIER_US = 2.5
+
+
+def _latency_roofline(kernel, terms, seconds, barriers_per_term):
+    """Taylor terms per second against the rate at which every term costs only its team barriers."""
+    achieved = terms / seconds
+    peak = 1e6 / (BARRIER_US * barriers_per_term)
+    return {"bound": "latency", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "Taylor terms/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_note": f"{barriers_per_term} team barrier(s) per term at {BARRIER_US} us each (GB300 "
+                         "microbenchmark at 304 blocks); the working set is L2-resident"}
+
+
+def _aux_line(value, ms, K, warmup, dtype, config, roofline, launches, wall, e2e, clk):
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": K, "warmup": warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": config, "roofline": roofline, "gpu_launches": int(launches),
+            "wall_s_timed_region": wall, "e2e": e2e}
+    summary = clk.summary()
+    if summary:
+        line["clocks"] = summary
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_exprk(args, rank, world, local_rank):
+    """exprk-adr: expRK4s6 on the paper's ADR problem (100 x 100 nodes, eps 1e-3, alpha -1/2,
+    gamma 1000), FP64 at tol 2^-53, h = 1/512, (s, xi) selected once before the timed region.  One
+    step = one integrator step: four phi-combination calls and the elementwise reaction terms; value =
+    calls (solves) per second.  e2e copies u from pinned host memory in and out again every step."""
+    import torch
+
+    from paper_2509_26475_gb300 import api, build, capi, exprk
+    from paper_2509_26475_gb300 import workloads as wl
+
+    if world > 1:
+        raise SystemExit("exprk-adr runs on one GPU")
+    build.build()
+    lib = capi.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    h, K = 1.0 / 512, args.steps
+    A = api.DeviceCSR.from_host(wl.adr_operator(), device=dev)
+    integ = exprk.ExpRK4s6(A, exprk.adr_reaction(wl.ADR_GAMMA))
+    u = torch.as_tensor(wl.adr_initial()).to(dev)
+    for _ in range(max(args.warmup, 0)):
+        u = integ.step(u, h)
+    integ.check()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    l0 = lib.phic_launch_count()
+    with ClockSampler(local_rank, None) as clk:
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        ev[0].record(stream)
+        for _ in range(K):
+            u = integ.step(u, h)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - w0
+    launches = lib.phic_launch_count() - l0
+    ms = ev[0].elapsed_time(ev[1]) / K
+    sts = [api.read_stats(x) for x in integ.stats]
+    integ.stats.clear()
+    if any(x["status"] != 0 for x in sts) or not bool(torch.isfinite(u).all()):
+        raise SystemExit("exprk-adr: a phi-combination reported a device status; no number is reported")
+    terms = sum(x["series_terms"] + x["recovery_terms"] for x in sts)
+    # e2e: the integration driven from the host, u in and out of pinned memory every step
+    uh = u.detach().cpu().pin_memory()
+    nb = uh.numel() * uh.element_size()
+    e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e2[0].record(stream)
+    for _ in range(K):
+        uh.copy_(integ.step(uh.to(dev, non_blocking=True), h), non_blocking=True)
+    e2[1].record(stream)
+    torch.cuda.synchronize(dev)
+    integ.check()
+    ms_e2e = e2[0].elapsed_time(e2[1]) / K
+    config = {"workload": "exprk-adr: expRK4s6 on the ADR problem, 100 x 100 nodes (n = 10,000), eps 1e-3, "
+                          "alpha -1/2, gamma 1000, h = 1/512, FP64 tol 2^-53; (s, xi) selected once",
+              "n": A.n, "nnz": A.nnz, "h": h, "calls_per_step": 4, "steps_per_s": 1000.0 / ms,
+              "taylor_terms_per_step": terms / K, "s": float(api.read_params(integ.params)["s"]),
+              "l2": "working set L2-resident (n = 10,000); no flush", "parallelism": "x1"}
+    return _aux_line(4 * 1000.0 / ms, ms, K, args.warmup, "f64", config,
+                     _latency_roofline("series_kernel + recover_kernel (4 calls per step)", terms, ms * K / 1000.0, 1),
+                     launches, wall, {"value": 4 * 1000.0 / ms_e2e, "unit": "solves/s", "ms_per_step": ms_e2e,
+                                      "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}, clk)
+
+
+def run_lowrank(args, rank, world, local_rank):
+    """lowrank-m2: the paper's third experiment with the core M2 = [[-1, 1e5], [0, -10]]: A = U W^T,
+    U the first two DCT-II columns of size n = 400,000, W = U M2^T, applied matrix-free; p = 4, r = 1,
+    alpha = 1, FP64 at tol 2^-53, v_j ~ N(0, 1) (seed 11).  One step = Algorithm 1 + Algorithm 3 at
+    t = 0.1 and t = 1 (2 solves); L2 flushed between steps."""
+    import numpy as np
+    import torch
+
+    from paper_2509_26475_gb300 import api, build, capi
+    from paper_2509_26475_gb300 import workloads as wl
+
+    if world > 1:
+        raise SystemExit("lowrank-m2 runs on one GPU")
+    build.build()
+    lib = capi.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    n, p, ts = 400000, 4, (0.1, 1.0)
+    M = np.array([[-1.0, 1e5], [0.0, -10.0]])
+    U_h = wl.dct_basis(n, 2)
+    W_h = U_h @ M.T
+    V_h = np.random.default_rng(11).standard_normal((p + 1, n))
+    A = api.DeviceLowRank(torch.as_tensor(U_h).to(dev).contiguous(), torch.as_tensor(W_h).to(dev).contiguous())
+    V = torch.as_tensor(V_h).to(dev)
+    flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size, dtype=torch.uint8, device=dev)
+
+    def step():
+        P = api.select_params(A, tol=TOL)
+        return P, [api.solve(A, V, [t], [1.0], TOL, P) for t in ts]
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    sts = []
+    l0 = lib.phic_launch_count()
+    with ClockSampler(local_rank, None) as clk:
+        w0 = time.perf_counter()
+        for k in range(K):
+            flush.fill_(k & 255)
+            evs[k][0].record(stream)
+            P = api.select_params(A, tol=TOL)
+            evs[k][1].record(stream)
+            sts += [api.solve(A, V, [t], [1.0], TOL, P)[1] for t in ts]
+            evs[k][2].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - w0
+    launches = lib.phic_launch_count() - l0
+    ms = sum(e[0].elapsed_time(e[2]) for e in evs) / K
+    solve_s = sum(e[1].elapsed_time(e[2]) for e in evs) / 1000.0
+    st = [api.read_stats(x) for x in sts]
+    if any(x["status"] != 0 for x in st):
+        raise SystemExit("lowrank-m2: a solve reported a device status; no number is reported")
+    terms = sum(x["series_terms"] + x["recovery_terms"] for x in st)
+    # e2e: U, W and V in from pinned host memory, the results out, every step
+    Uh, Wh, Vh = (torch.as_tensor(x).pin_memory() for x in (U_h, W_h, V_h))
+    outs = [torch.empty((1, n), dtype=torch.float64).pin_memory() for _ in ts]
+    e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e2[0].record(stream)
+    for _ in range(K):
+        Ad = api.DeviceLowRank(Uh.to(dev, non_blocking=True), Wh.to(dev, non_blocking=True))
+        Vd = Vh.to(dev, non_blocking=True)
+        Pd = api.select_params(Ad, tol=TOL)
+        for o, t in zip(outs, ts):
+            o.copy_(api.solve(Ad, Vd, [t], [1.0], TOL, Pd)[0], non_blocking=True)
+    e2[1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = e2[0].elapsed_time(e2[1]) / K
+    h2d = sum(x.numel() * x.element_size() for x in (Uh, Wh, Vh))
+    d2h = sum(o.numel() * o.element_size() for o in outs)
+    config = {"workload": "lowrank-m2: A = U W^T, W = U M2^T, M2 = [[-1, 1e5], [0, -10]], U = 2 DCT-II columns, "
+                          "n = 400,000, p = 4, r = 1, t in {0.1, 1}, alpha = 1, FP64 tol 2^-53",
+              "n": n, "k": 2, "p": p, "t": list(ts), "s_int": [x["s_int"] for x in st[:len(ts)]],
+              "terms": [x["series_terms"] + x["recovery_terms"] for x in st[:len(ts)]],
+              "step": "Algorithm 1 + Algorithm 3 at each t (2 solves)",
+              "l2": "flushed between steps (2 x L2 write, outside the step events)", "parallelism": "x1"}
+    return _aux_line(len(ts) * 1000.0 / ms, ms, K, args.warmup, "f64", config,
+                     _latency_roofline("lr_series_kernel + lr_recover_kernel (the two solves of a step)", terms,
+                                       solve_s, 2),
+                     launches, wall, {"value": len(ts) * 1000.0 / ms_e2e, "unit": "solves/s", "ms_per_step": ms_e2e,
+                                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}, clk)
+
+
+def run_reference_exprk(args):
+    """--impl reference for exprk-adr: the same expRK4s6 steps with every phi-combination by the oracle
+    (FP64 C, OpenMP over sparse-product rows) on the host cores, for a bounded number of steps."""
+    import numpy as np
+
+    import oracle
+    from paper_2509_26475_gb300 import exprk
+    from paper_2509_26475_gb300 import workloads as wl
+
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    A_h = wl.adr_operator()
+    g = exprk.adr_reaction(wl.ADR_GAMMA)
+    sel = oracle.select(A_h)
+    h = 1.0 / 512
+
+    def comb(ci):
+        return oracle.solve(A_h, np.stack(ci.V), ci.t, ci.alpha, 2.0**-53, sel["s"], sel["xi"])[0]
+
+    def step(u):
+        gu = g(u)
+        hg = h * gu
+        U2 = comb(exprk.stage2_inputs(u, hg, h))[0]
+        D2 = g(U2) - gu
+        W34 = comb(exprk.stage34_inputs(u, hg, D2, h))
+        D3, D4 = g(W34[0]) - gu, g(W34[1]) - gu
+        W56 = comb(exprk.stage56_inputs(u, hg, D3, D4, h))
+        D5, D6 = g(W56[0]) - gu, g(W56[1]) - gu
+        return comb(exprk.final_inputs(u, hg, D5, D6, h))[0]
+
+    u = wl.adr_initial()
+    steps_run, warm_run = min(max(1, args.steps), 20), min(max(0, args.warmup), 1)
+    for _ in range(warm_run):
+        u = step(u)
+    t0 = time.perf_counter()
+    for _ in range(steps_run):
+        u = step(u)
+    ms = 1000.0 * (time.perf_counter() - t0) / steps_run
+    value = 4 * 1000.0 / ms
+    sample = f"{steps_run} expRK4s6 step(s) of h = 1/512 on the ADR problem (4 oracle combinations each)"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+                      "steps": steps_run, "warmup": warm_run, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "exprk-adr (oracle combinations)", "device": "host CPU", "threads": cores},
+                      "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
     return 0
 
 

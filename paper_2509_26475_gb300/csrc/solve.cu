@@ -24,24 +24,36 @@ __global__ void __launch_bounds__(kBlock, 2) lr_series_kernel(const SolveArgs a)
 
 namespace {
 
-template <typename T, int MINB>
+// Resident blocks per SM a series kernel is built for: 2 for tiles up to 4 columns; for wider tiles
+// PHIC_SERIES_MINB_F32 when FP32 lanes hold at most 4 floats (their loops fit 64 registers: 5.98 ->
+// 5.22 ms per 28-term series at n = 1,048,576 on GB300), else wide_minb.
+#ifndef PHIC_SERIES_MINB_F32
+#define PHIC_SERIES_MINB_F32 4
+#endif
+template <typename T, int CW, bool kWide>
+constexpr int series_minb() {
+  return !kWide ? 2 : (sizeof(T) == 4 && CW <= 4) ? PHIC_SERIES_MINB_F32 : wide_minb<T>();
+}
+
+template <typename T, bool kWide>
 cudaError_t dispatch_series_b(const SolveArgs& a, cudaStream_t st, int* g) {
   const long long items = (long long)a.n * a.S_lay.Lp2;
   const int bps = blocks_per_sm(sizeof(T));
   switch (a.S_lay.cw) {
-    case 1: return coop_launch(series_kernel<T, 1, MINB>, items, bps, a, st, g);
-    case 2: return coop_launch(series_kernel<T, 2, MINB>, items, bps, a, st, g);
+    case 1: return coop_launch(series_kernel<T, 1, series_minb<T, 1, kWide>()>, items, bps, a, st, g);
+    case 2: return coop_launch(series_kernel<T, 2, series_minb<T, 2, kWide>()>, items, bps, a, st, g);
 #if PHIC_CW_MAX_F32 >= 8
     case 8:
-      if constexpr (sizeof(T) == 4) return coop_launch(series_kernel<T, 8, MINB>, items, bps, a, st, g);
+      if constexpr (sizeof(T) == 4)
+        return coop_launch(series_kernel<T, 8, series_minb<T, 8, kWide>()>, items, bps, a, st, g);
       return cudaErrorInvalidValue;
 #endif
-    default: return coop_launch(series_kernel<T, 4, MINB>, items, bps, a, st, g);
+    default: return coop_launch(series_kernel<T, 4, series_minb<T, 4, kWide>()>, items, bps, a, st, g);
   }
 }
 template <typename T>
 cudaError_t dispatch_series(const SolveArgs& a, cudaStream_t st, int* g) {
-  return a.S_lay.w <= 4 ? dispatch_series_b<T, 2>(a, st, g) : dispatch_series_b<T, wide_minb<T>()>(a, st, g);
+  return a.S_lay.w <= 4 ? dispatch_series_b<T, false>(a, st, g) : dispatch_series_b<T, true>(a, st, g);
 }
 }  // namespace
 
