@@ -847,8 +847,10 @@ def _aux_line(value, ms, K, warmup, dtype, config, roofline, launches, wall, e2e
 def run_exprk(args, rank, world, local_rank):
     """exprk-adr: expRK4s6 on the paper's ADR problem (100 x 100 nodes, eps 1e-3, alpha -1/2,
     gamma 1000), FP64 at tol 2^-53, h = 1/512, (s, xi) selected once before the timed region.  One
-    step = one integrator step: four phi-combination calls and the elementwise reaction terms; value =
-    calls (solves) per second.  e2e copies u from pinned host memory in and out again every step."""
+    step = one integrator step: four phi-combination calls and the elementwise reaction terms, captured
+    once as a CUDA graph and replayed; value = calls (solves) per second.  The same steps issued eagerly
+    from Python are timed beside it (config).  e2e copies u from pinned host memory in and out again
+    every step."""
     import torch
 
     from paper_2509_26475_gb300 import api, build, capi, exprk
@@ -865,47 +867,68 @@ def run_exprk(args, rank, world, local_rank):
     A = api.DeviceCSR.from_host(wl.adr_operator(), device=dev)
     integ = exprk.ExpRK4s6(A, exprk.adr_reaction(wl.ADR_GAMMA))
     u = torch.as_tensor(wl.adr_initial()).to(dev)
+
+    def timed(fn):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        return ev[0].elapsed_time(ev[1]) / K
+
+    # eager steps (Python issues every call)
     for _ in range(max(args.warmup, 0)):
         u = integ.step(u, h)
     integ.check()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    l0 = lib.phic_launch_count()
-    with ClockSampler(local_rank, None) as clk:
-        torch.cuda.synchronize(dev)
-        w0 = time.perf_counter()
-        ev[0].record(stream)
+    state = {"u": u}
+
+    def eager():
         for _ in range(K):
-            u = integ.step(u, h)
-        ev[1].record(stream)
-        torch.cuda.synchronize(dev)
-        wall = time.perf_counter() - w0
-    launches = lib.phic_launch_count() - l0
-    ms = ev[0].elapsed_time(ev[1]) / K
+            state["u"] = integ.step(state["u"], h)
+
+    ms_eager = timed(eager)
     sts = [api.read_stats(x) for x in integ.stats]
-    integ.stats.clear()
-    if any(x["status"] != 0 for x in sts) or not bool(torch.isfinite(u).all()):
+    integ.check()
+    # the captured step, replayed
+    u = state["u"]
+    l0 = lib.phic_launch_count()
+    sg = integ.capture(u, h)
+    per_step = lib.phic_launch_count() - l0 - 8  # capture() runs one eager warm-up step (8 launches) first
+    sg.replay(max(args.warmup, 1))
+    sg.check()
+    with ClockSampler(local_rank, None) as clk:
+        w0 = time.perf_counter()
+        ms = timed(lambda: sg.replay(K))
+        wall = time.perf_counter() - w0
+    sg.check()
+    last = [api.read_stats(x) for x in sg.stats]  # the four calls of the last replayed step
+    if any(x["status"] != 0 for x in sts + last) or not bool(torch.isfinite(u).all()):
         raise SystemExit("exprk-adr: a phi-combination reported a device status; no number is reported")
-    terms = sum(x["series_terms"] + x["recovery_terms"] for x in sts)
+    terms = sum(x["series_terms"] + x["recovery_terms"] for x in last)
     # e2e: the integration driven from the host, u in and out of pinned memory every step
     uh = u.detach().cpu().pin_memory()
     nb = uh.numel() * uh.element_size()
-    e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    e2[0].record(stream)
-    for _ in range(K):
-        uh.copy_(integ.step(uh.to(dev, non_blocking=True), h), non_blocking=True)
-    e2[1].record(stream)
-    torch.cuda.synchronize(dev)
-    integ.check()
-    ms_e2e = e2[0].elapsed_time(e2[1]) / K
+
+    def host_loop():
+        for _ in range(K):
+            u.copy_(uh, non_blocking=True)
+            sg.replay()
+            uh.copy_(u, non_blocking=True)
+
+    ms_e2e = timed(host_loop)
+    sg.check()
     config = {"workload": "exprk-adr: expRK4s6 on the ADR problem, 100 x 100 nodes (n = 10,000), eps 1e-3, "
-                          "alpha -1/2, gamma 1000, h = 1/512, FP64 tol 2^-53; (s, xi) selected once",
+                          "alpha -1/2, gamma 1000, h = 1/512, FP64 tol 2^-53; (s, xi) selected once; each step "
+                          "one CUDA graph replay",
               "n": A.n, "nnz": A.nnz, "h": h, "calls_per_step": 4, "steps_per_s": 1000.0 / ms,
-              "taylor_terms_per_step": terms / K, "s": float(api.read_params(integ.params)["s"]),
+              "eager_steps_per_s": 1000.0 / ms_eager, "taylor_terms_per_step": terms,
+              "launches_per_step": per_step, "s": float(api.read_params(integ.params)["s"]),
               "l2": "working set L2-resident (n = 10,000); no flush", "parallelism": "x1"}
     return _aux_line(4 * 1000.0 / ms, ms, K, args.warmup, "f64", config,
-                     _latency_roofline("series_kernel + recover_kernel (4 calls per step)", terms, ms * K / 1000.0, 1),
-                     launches, wall, {"value": 4 * 1000.0 / ms_e2e, "unit": "solves/s", "ms_per_step": ms_e2e,
-                                      "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}, clk)
+                     _latency_roofline("series_kernel + recover_kernel (4 calls per step)", terms * K, ms * K / 1000.0, 1),
+                     per_step * K, wall, {"value": 4 * 1000.0 / ms_e2e, "unit": "solves/s", "ms_per_step": ms_e2e,
+                                          "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}, clk)
 
 
 def run_lowrank(args, rank, world, local_rank):

@@ -78,22 +78,29 @@ cudaError_t launch_lr_series(const SolveArgs& a, int prec, cudaStream_t st) {
 cudaError_t launch_series(const SolveArgs& a, int prec, cudaStream_t st, int* grid_out) {
   return prec == PHIC_F32 ? dispatch_series<float>(a, st, grid_out) : dispatch_series<double>(a, st, grid_out);
 }
+// Odd widths from 3 to 31 columns are padded by one column (computed as zero), so that a lane carries
+// two or more values with vector loads, and a row needs half the lanes.
+#ifndef PHIC_PAD_ODD
+#define PHIC_PAD_ODD 1
+#endif
+
 TileLayout pick_layout(int w, int elem_bytes) {
   const int cw_max = elem_bytes == 4 ? PHIC_CW_MAX_F32 : PHIC_CW_MAX;
+  const int wp = (PHIC_PAD_ODD && w >= 3 && w < 32 && (w & 1)) ? w + 1 : w;
   TileLayout t;
   t.w = w;
-  if (cw_max >= 8 && w % 8 == 0 && w / 8 <= 32) {
+  if (cw_max >= 8 && wp % 8 == 0 && wp / 8 <= 32) {
     t.cw = 8;
-    t.ws = w;
-  } else if (cw_max >= 4 && w % 4 == 0 && w / 4 <= 32) {
+    t.ws = wp;
+  } else if (cw_max >= 4 && wp % 4 == 0 && wp / 4 <= 32) {
     t.cw = 4;
-    t.ws = w;
-  } else if (cw_max >= 2 && w % 2 == 0 && w / 2 <= 32) {
+    t.ws = wp;
+  } else if (cw_max >= 2 && wp % 2 == 0 && wp / 2 <= 32) {
     t.cw = 2;
-    t.ws = w;
-  } else if (w <= 32) {
+    t.ws = wp;
+  } else if (wp <= 32) {
     t.cw = 1;
-    t.ws = w;
+    t.ws = wp;
   } else {
     t.cw = 4;
     t.ws = (w + 3) / 4 * 4;

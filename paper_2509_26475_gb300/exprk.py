@@ -95,13 +95,52 @@ class ExpRK4s6:
     def check(self):
         """Synchronises and raises if any call reported a device status."""
         torch.cuda.synchronize()
-        for st in self.stats:
-            s = api.read_stats(st)["status"]
-            if s != 0:
-                from . import capi
-
-                capi.check(s, "expRK4s6 stage")
+        _check_stats(self.stats)
         self.stats.clear()
+
+    def capture(self, u: torch.Tensor, h: float) -> "StepGraph":
+        """Records one step of size h on the device vector u as a CUDA graph: each replay of the result
+        advances u in place (u <- step(u)) with the four phi-combination launches, the reaction terms and
+        the copy back into u, and no host work per step beyond the replay call.  (s, xi), t and alpha
+        are fixed at capture."""
+        cur = torch.cuda.current_stream(u.device)
+        side = torch.cuda.Stream(device=u.device)
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            self.step(u.clone(), h)  # warm-up outside the capture: workspaces and allocator state
+            side.synchronize()
+            self.check()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                u.copy_(self.step(u, h))
+        cur.wait_stream(side)
+        stats, self.stats = self.stats, []
+        return StepGraph(g, stats)
+
+
+class StepGraph:
+    """A captured expRK4s6 step (ExpRK4s6.capture)."""
+
+    def __init__(self, graph, stats):
+        self.graph, self.stats = graph, stats
+
+    def replay(self, steps: int = 1):
+        for _ in range(steps):
+            self.graph.replay()
+
+    def check(self):
+        """Synchronises and raises if a call of the last replay reported a device status."""
+        torch.cuda.synchronize()
+        _check_stats(self.stats)
+
+
+def _check_stats(stats):
+    for st in stats:
+        s = api.read_stats(st)["status"]
+        if s != 0:
+            from . import capi
+
+            capi.check(s, "expRK4s6 stage")
 
 
 def adr_reaction(gamma: float = 1000.0):

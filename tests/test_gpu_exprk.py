@@ -66,3 +66,20 @@ def test_adr_fourth_order_by_step_halving():
     orders = [math.log2(diffs[k] / diffs[k + 1]) for k in range(2)]
     print("ADR expRK4s6 step-halving differences", diffs, "orders", orders)
     assert all(3.5 <= o <= 4.6 for o in orders), (diffs, orders)
+
+
+def test_captured_step_replays_the_eager_steps():
+    """A step captured as a CUDA graph and replayed gives bit for bit the eager steps."""
+    A = api.DeviceCSR.from_host(wl.adr_operator(100))
+    drv = exprk.ExpRK4s6(A, exprk.adr_reaction())
+    h = 1.0 / 512
+    u0 = torch.as_tensor(wl.adr_initial(100)).cuda()
+    ue = u0.clone()
+    for _ in range(3):
+        ue = drv.step(ue, h)
+    drv.check()
+    ug = u0.clone()
+    sg = drv.capture(ug, h)
+    sg.replay(3)
+    sg.check()
+    assert torch.equal(ug, ue)
