@@ -5,17 +5,22 @@
 
 namespace phic {
 
+// dyn_smem bytes of dynamic shared memory per block (the kernel's attribute is raised to allow them).
 template <typename K>
 inline cudaError_t coop_launch(K kernel, long long items, int max_per_sm, const SolveArgs& a, cudaStream_t st,
-                               int* grid_out, int max_grid = 1 << 30) {
+                               int* grid_out, int max_grid = 1 << 30, size_t dyn_smem = 0) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  if (dyn_smem > 0) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    if (e != cudaSuccess) return e;
+  }
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, dyn_smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   if (per_sm > max_per_sm) per_sm = max_per_sm;
@@ -26,7 +31,7 @@ inline cudaError_t coop_launch(K kernel, long long items, int max_per_sm, const 
   if (grid_out) *grid_out = (int)grid;
   void* args[] = {const_cast<SolveArgs*>(&a)};
   count_launch();
-  return cudaLaunchCooperativeKernel((const void*)kernel, dim3((unsigned)grid), dim3(kBlock), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void*)kernel, dim3((unsigned)grid), dim3(kBlock), args, dyn_smem, st);
 }
 
 // Residency the kernels are built for: 2 blocks per SM for tiles up to 4 columns; for wider tiles the

@@ -938,9 +938,13 @@ __device__ __forceinline__ void jt_power_coeffs(RecoverScalars<T>& rs, const Sol
 // max_steps outer steps j; it writes the output once j reaches s_int - 1, and otherwise records in
 // a.state where the next slice resumes.  Returns 1 once the solve is finished (output written or an
 // error recorded).
+//
+// E, the sum of one step's terms, is private to a step and to the rows of each team member: with e_sm
+// (shared memory of at least e_bytes) a member whose rows fit keeps its E there, off DRAM and L2.
 template <typename T, int CW, bool LR = false, bool kSplit = false>
 __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, RecoverSmem<T>& sm, int& phase,
-                                            int max_steps, LowRankSmem<T>* lz = nullptr) {
+                                            int max_steps, LowRankSmem<T>* lz = nullptr, T* e_sm = nullptr,
+                                            unsigned e_bytes = 0) {
   RecoverScalars<T>& sc = sm.sc;
   LoopCtl& lc = sm.lc;
   WarpParts& wp = sm.wp;
@@ -1016,10 +1020,17 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   const CsrEnt<T>* __restrict__ ent = static_cast<const CsrEnt<T>*>(a.A1);
   const T* __restrict__ S = static_cast<const T*>(a.S);
   const T* __restrict__ Vin = static_cast<const T*>(a.Vin);
-  T* __restrict__ E = static_cast<T*>(a.E);
   const BlockRows br(n, L.Lp2, tm);
   const int lmask = L.Lp2 - 1;
   const int c0 = (threadIdx.x & lmask) * CW;
+  // E of this member's rows, in shared memory when they fit (every thread reads back only the elements it
+  // wrote, so no barrier orders them).  Either way row `row` is at E + row ws: for shared memory E is
+  // the generic address br.r0 rows before the buffer, so that the loops index both cases alike and every
+  // access they make lies inside it.
+  const bool e_local = e_sm != nullptr && (size_t)(br.r1 - br.r0) * L.ws * sizeof(T) <= e_bytes;
+  T* __restrict__ E = e_local ? reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(e_sm) -
+                                                     (uintptr_t)br.r0 * L.ws * sizeof(T))
+                              : static_cast<T*>(a.E);
   // per-column facts of this thread's lane, computed where used (so that none of them stays live across
   // the Taylor loop): column c0 + j is live when below w; block p of F when at least r; combination i
   auto col_live = [&](int j) { return c0 + j < L.w; };
