@@ -1009,9 +1009,20 @@ def run_lowrank(args, rank, world, local_rank):
               "terms": [x["series_terms"] + x["recovery_terms"] for x in st[:len(ts)]],
               "step": "Algorithm 1 + Algorithm 3 at each t (2 solves)",
               "l2": "flushed between steps (2 x L2 write, outside the step events)", "parallelism": "x1"}
-    return _aux_line(len(ts) * 1000.0 / ms, ms, K, args.warmup, "f64", config,
-                     _latency_roofline("lr_series_kernel + lr_recover_kernel (the two solves of a step)", terms,
-                                       solve_s, 2),
+    # FP64 flops of the two solves: per product with A = U W^T, W^T X and U Z (4 n k w), plus the
+    # series update (about 4 n w per term) or the recovery update (about 3 n w per term)
+    ws_, wf_ = (p + 1) * 1, 2 * 1
+    flops = sum(x["series_terms"] * (4 * n * 2 + 4 * n) * ws_ + x["recovery_terms"] * (4 * n * 2 + 3 * n) * wf_
+                for x in st)
+    achieved = flops / solve_s / 1e9
+    roof = {"bound": "alu", "kernel": "lr_series_kernel + lr_recover_kernel (the two solves of a step)",
+            "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "FP64 GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+            "peak_note": "FP64 pipe: 2 FMA/clk/SM x 2 flop x 152 SMs x 2070 MHz; achieved counts (4 n k + 4 n) w "
+                         "flops per series term and (4 n k + 3 n) w per recovery term, k = 2; the working set is "
+                         "L2-resident",
+            "taylor_terms_per_s": terms / solve_s}
+    return _aux_line(len(ts) * 1000.0 / ms, ms, K, args.warmup, "f64", config, roof,
                      launches, wall, {"value": len(ts) * 1000.0 / ms_e2e, "unit": "solves/s", "ms_per_step": ms_e2e,
                                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}, clk)
 
