@@ -41,10 +41,13 @@ __device__ __noinline__ void select_call(const SelectArgs& a, Team& tm, SelShare
 
 template <typename T>
 __device__ __forceinline__ void run_series(const SolveArgs& a, Team& tm, BatchSmem& u, int& phase);
+// Lane widths follow pick_layout: FP64 tiles take 1 or 2 columns per lane up to 32 columns and 4
+// beyond; FP32 tiles 1, 2, 4 or 8.
 template <>
 __device__ __forceinline__ void run_series<double>(const SolveArgs& a, Team& tm, BatchSmem& u, int& phase) {
   if (a.S_lay.cw == 1) series_call<double, 1>(a, tm, u.s64, phase);
-  else series_call<double, 2>(a, tm, u.s64, phase);
+  else if (a.S_lay.cw == 2) series_call<double, 2>(a, tm, u.s64, phase);
+  else series_call<double, 4>(a, tm, u.s64, phase);
 }
 template <>
 __device__ __forceinline__ void run_series<float>(const SolveArgs& a, Team& tm, BatchSmem& u, int& phase) {
@@ -62,7 +65,8 @@ template <>
 __device__ __forceinline__ void run_recover<double>(const SolveArgs& a, Team& tm, BatchSmem& u, int& phase,
                                                      int steps) {
   if (a.F_lay.cw == 1) recover_call<double, 1>(a, tm, u.r64, phase, steps);
-  else recover_call<double, 2>(a, tm, u.r64, phase, steps);
+  else if (a.F_lay.cw == 2) recover_call<double, 2>(a, tm, u.r64, phase, steps);
+  else recover_call<double, 4>(a, tm, u.r64, phase, steps);
 }
 template <>
 __device__ __forceinline__ void run_recover<float>(const SolveArgs& a, Team& tm, BatchSmem& u, int& phase,

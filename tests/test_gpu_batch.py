@@ -71,6 +71,29 @@ def test_batch_equals_single_instance_bitwise():
         assert torch.equal(it.W, W), k
 
 
+def test_wide_tiles_equal_single_instance_bitwise():
+    """Series tiles of 36 to 128 columns (4 or 8 columns per lane) in both precisions, with the
+    recoveries of 8 and 16 columns: the batched solve equals the single-instance solve bit for bit."""
+    insts = []
+    for k, (p, r, prec) in enumerate([(15, 8, "f64"), (10, 4, "f64"), (8, 4, "f32"), (15, 8, "f32")]):
+        A = wl.convection_diffusion(20 + 3 * k, 2, 5.0)
+        rng = np.random.default_rng(70 + k)
+        insts.append(dict(A=A, V=rng.standard_normal((p + 1, A.n)), t=np.linspace(8e-3, 1.6e-2, r),
+                          alpha=np.linspace(0.6, 1.2, r), tol=2.0**-53 if prec == "f64" else 2.0**-24, prec=prec,
+                          p=p, r=r))
+    devs = [_dev(x) for x in insts]
+    singles = [_single(x, *d) for x, d in zip(insts, devs)]
+    items = _items(insts, devs, params=[s[0] for s in singles])
+    b = api.Batch(items, config={"rows_per_cta": 256, "blocks_per_sm": 2})
+    b.launch()
+    torch.cuda.synchronize()
+    for k, (it, (P, W, st)) in enumerate(zip(items, singles)):
+        bs = api.read_stats(it.stats)
+        assert bs["status"] == 0 and st["status"] == 0, (k, bs, st)
+        assert bs["s_int"] >= 2 and bs["recovery_terms"] == st["recovery_terms"], (k, bs, st)
+        assert torch.equal(it.W, W), k
+
+
 def test_batch_residency_and_team_size_do_not_change_results():
     insts = _instances(6, 8, precision="f64")
     devs = [_dev(x) for x in insts]
