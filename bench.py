@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=1000, help="serve: number of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--no-tune", action="store_true", help="batch512: skip the autotuner (default shape)")
+    ap.add_argument("--profile-batch", type=int, default=None, metavar="COUNT",
+                    help="profiler target: the first COUNT instances of batch512 in one batched launch (twice, "
+                         "default shape), no timing and no JSON line")
     ap.add_argument("--profile-solve", type=float, default=None, metavar="H",
                     help="profiler target: Algorithm 1 and two Algorithm 3 solves of the workload at step H, "
                          "no timing and no JSON line")
@@ -98,6 +101,29 @@ def profile_solve(h: float) -> int:
         W, st = api.solve(A, V, t_of(h), alpha, TOL, P, check=True)
     print(api.read_stats(st))
     return 0
+
+
+def profile_batch(count: int) -> int:
+    """A short launch sequence for profilers: the first `count` instances of the batching workload (each
+    Algorithm 1 + 3), one batched launch twice at 4096 rows per CTA and 3 blocks per SM."""
+    import torch
+
+    from paper_2509_26475_gb300 import api
+
+    insts = batch_workload("mixed")[:max(1, count)]
+    items = []
+    for x in insts:
+        dt = torch.float32 if x["prec"] == "f32" else torch.float64
+        A = api.DeviceCSR.from_host(x["A"], dtype=dt)
+        items.append(api.BatchItem(A, torch.as_tensor(x["V"]).to(dt).cuda(), x["t"], x["alpha"], tol=x["tol"],
+                                   select=True))
+    b = api.Batch(items, config={"rows_per_cta": 4096, "blocks_per_sm": 3})
+    for _ in range(2):
+        b.launch()
+    torch.cuda.synchronize()
+    bad = [i for i, st in enumerate(b.stats()) if st["status"] != 0]
+    print({"rows": sum(x["A"].n for x in insts), "bad": bad, **b.info()})
+    return 1 if bad else 0
 
 
 def dist_env():
@@ -294,6 +320,8 @@ def main():
         return run_reference(args, rank, world)
     if args.profile_solve is not None:
         return profile_solve(args.profile_solve)
+    if args.profile_batch is not None:
+        return profile_batch(args.profile_batch)
     if WORKLOAD == "batch512":
         return run_batch(args, rank, world, local_rank)
     if WORKLOAD == "serve":

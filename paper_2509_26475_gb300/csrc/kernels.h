@@ -158,6 +158,22 @@ int blocks_per_sm(int elem_bytes);
 unsigned long long spin_limit_ns();
 // Enqueues a one-block kernel that writes the number of unfinished solves of the batch to *out.
 cudaError_t launch_batch_pending(const BatchInst* inst, int count, int* out, cudaStream_t st);
+// Infinity norms of a batch's operators, for the planner's estimate of Algorithm 1's s: chunk c covers
+// rows [r0, r0 + rows_per_chunk) of its item; out_bits[item] (zeroed by the caller) receives the bits of
+// max_i sum_j |a_ij| (a nonnegative double, so its bits order like the value).  Rows whose bounds are
+// not in [0, nnz] are skipped.  One block per chunk.
+struct NormItem {
+  const int* rowptr;
+  const void* vals;
+  long long nnz;
+  int n, f32, rows_per_chunk, pad;
+};
+struct NormChunk {
+  int item;
+  int r0;
+};
+cudaError_t launch_batch_norms(const NormItem* items, const NormChunk* chunks, int nchunks,
+                               unsigned long long* out_bits, cudaStream_t st);
 // Enqueues a kernel that copies, for each instance of a slice, its done flag, phic_stats and
 // phic_params into contiguous device arrays (for one small read-back).
 cudaError_t launch_batch_collect(const BatchInst* inst, int count, int* done, phic_stats* stats, phic_params* params,
