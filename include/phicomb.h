@@ -259,7 +259,7 @@ typedef struct {
   phic_stats* stats;       /* device or NULL, as in phic_solve */
   const double* v_select;  /* device unit vector for Algorithm 1, or NULL (splitmix64 of the options' seed) */
   double tol;              /* truncation tolerance, as in phic_solve */
-  double s_hint;           /* host estimate of s for the planner's cost model only (<= 0: one scaling step) */
+  double s_hint;           /* estimate of s for the planner's cost model only; <= 0: see phic_batch_create */
   double t[PHIC_MAX_R];    /* abscissae t_1..t_r (host copy) */
   double alpha[PHIC_MAX_R];/* weights alpha_1..alpha_r (host copy) */
 } phic_batch_item;
@@ -296,8 +296,12 @@ phic_status phic_batch_workspace_size(const phic_batch_item* items, int32_t coun
 
 /* Checks the items (host side, as phic_solve does), lays out ws (device, 256-byte aligned), plans the
  * teams and the schedule for cfg (NULL: defaults) and copies the instance table and the schedule into
- * ws on `stream`, synchronising `stream` once before returning (set-up call, not for capture).  items
- * is read before the call returns.  *out receives the handle. */
+ * ws on `stream`, synchronising `stream` before returning (set-up call, not for capture).  items is
+ * read before the call returns.  *out receives the handle.
+ * An item with PHIC_BATCH_SELECT and a solve but no s_hint (<= 0) is planned with the hint
+ * ||A||_inf / (2 (tol m!)^(1/m)), m = opts->m: Algorithm 1's s = s0 f* / (tol m!)^(1/m) with s0 f*
+ * taken as ||A - xi I|| ~ ||A||_inf / 2.  The norms are computed on `stream` first, in ws.
+ * phic_batch_plan_host, which reads no device memory, uses s_hint as given (<= 0: one scaling step). */
 phic_status phic_batch_create(const phic_batch_item* items, int32_t count, const phic_select_opts* opts,
                               const phic_batch_config* cfg, void* ws, size_t ws_bytes, phic_stream_t stream,
                               phic_batch** out);

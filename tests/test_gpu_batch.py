@@ -200,3 +200,50 @@ def test_autotune_picks_a_candidate():
     assert best in [dict(c, max_steps=0) for c in cands]
     assert ms > 0.0
     assert all(api.read_stats(it.stats)["status"] == 0 for it in items)
+
+
+def test_planner_hints_from_operator_norms():
+    """Items that run Algorithm 1 without an s_hint are planned with ||A||_inf / (2 (tol m!)^(1/m)),
+    the norms taken on the device: the batch's plan equals the host planner's for the same hints
+    computed on the host (row sums in the same order, in FP64 of the stored values)."""
+    import ctypes
+    import math
+
+    insts = _instances(10, 23)
+    devs = [_dev(x) for x in insts]
+    items = _items(insts, devs, select=True)
+    b = api.Batch(items, config={"rows_per_cta": 1024, "blocks_per_sm": 2})
+    info = b.info()
+    m = b.opts.m
+    arr = api._item_array(items)
+    for k, x in enumerate(insts):
+        A = x["A"]
+        lens = np.diff(A.rowptr)
+        dt = np.float32 if x["prec"] == "f32" else np.float64
+        vals = np.abs(np.asarray(A.values).astype(dt)).astype(np.float64)
+        sums = np.zeros(A.n)
+        for q in range(int(lens.max())):  # entry q of every row, in the device's order
+            has = lens > q
+            sums[has] = sums[has] + vals[A.rowptr[:-1][has] + q]
+        theta = math.exp((math.log(x["tol"]) + math.lgamma(m + 1.0)) / m)
+        arr[k].s_hint = float(sums.max()) / (2.0 * theta)
+        assert arr[k].s_hint > 0.0
+    grid = info["grid"]
+    cfg = capi.phic_batch_config(1024, 2, 0, 0)
+    cap = info["entries"] + 8
+    team = (ctypes.c_int32 * len(items))()
+    ptr = (ctypes.c_int32 * (grid + 1))()
+    sched = (ctypes.c_int32 * (2 * cap))()
+    ent = ctypes.c_int64(0)
+    mk = ctypes.c_double(0.0)
+    st = capi.load().phic_batch_plan_host(arr, len(items), ctypes.byref(b.opts), ctypes.byref(cfg), grid, team, ptr,
+                                          sched, cap, ctypes.byref(ent), ctypes.byref(mk))
+    assert st == capi.PHIC_OK
+    assert ent.value == info["entries"]
+    assert mk.value == pytest.approx(info["est_makespan_us"], rel=1e-12)
+    # without the hints every instance counts as one outer step: a shorter estimate
+    for k in range(len(items)):
+        arr[k].s_hint = 0.0
+    st = capi.load().phic_batch_plan_host(arr, len(items), ctypes.byref(b.opts), ctypes.byref(cfg), grid, team, ptr,
+                                          sched, cap, ctypes.byref(ent), ctypes.byref(mk))
+    assert st == capi.PHIC_OK and mk.value < info["est_makespan_us"]
