@@ -200,8 +200,10 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
   int bad = 0;
 
   if (threadIdx.x == 0) {
+    // max_j log binom(m, j): at the middle index (both middle indices for odd m, in the same form as
+    // any j); neighbouring j differ by at least log(1 + 2/m), far above the rounding of lgamma
     double lmax = -INFINITY;
-    for (int j = 0; j <= m; ++j) lmax = fmax(lmax, lgamma(m + 1.0) - lgamma(j + 1.0) - lgamma(m - j + 1.0));
+    for (int j = m / 2; j <= (m + 1) / 2; ++j) lmax = fmax(lmax, lgamma(m + 1.0) - lgamma(j + 1.0) - lgamma(m - j + 1.0));
     sh.lmax = lmax;
     sh.gmax = a.delta * log(DBL_MAX);
     sh.gmin = a.delta * log(DBL_MIN);
