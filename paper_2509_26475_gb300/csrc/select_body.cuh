@@ -31,6 +31,32 @@ constexpr int kMaxM = 128;
 // Brent (1973, ch. 5) minimiser as a resumable state machine: after each function value it either
 // names the next abscissa to evaluate (u) or finishes.  Golden-section steps into the larger part of
 // the bracket, parabolic steps through the three best points when they are safe.
+// z^e for an integer e >= 0 by binary exponentiation (square and multiply) carried in double-double
+// arithmetic, Dekker's exact product through an FMA, and rounded once: within about an ulp of the exact
+// power, as a general pow, in at most 2 log2(e) double-double products.  Overflow returns the product
+// that overflowed (+-inf).
+__device__ __forceinline__ void dd_mul(double& ah, double& al, double bh, double bl) {
+  const double p = ah * bh;
+  if (!isfinite(p)) {
+    ah = p;
+    al = 0.0;
+    return;
+  }
+  const double e = fma(ah, bh, -p) + (ah * bl + al * bh);
+  const double s = p + e;
+  al = e - (s - p);
+  ah = s;
+}
+__device__ __forceinline__ double pow_int(double z, int e) {
+  double rh = 1.0, rl = 0.0, bh = z, bl = 0.0;
+  while (e > 0) {
+    if (e & 1) dd_mul(rh, rl, bh, bl);
+    e >>= 1;
+    if (e) dd_mul(bh, bl, bh, bl);
+  }
+  return isfinite(rh) ? rh + rl : rh;
+}
+
 struct BrentSM {
   double lo, hi;        // bracket
   double x, w, v;       // best, second best, previous second best
@@ -369,7 +395,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
     if (threadIdx.x <= m) {
       const int kk = threadIdx.x;
       const double z = -sh.br.u / sh.s0;
-      sh.coef[kk] = sh.binom[kk] * pow(z, (double)(m - kk));
+      sh.coef[kk] = sh.binom[kk] * pow_int(z, m - kk);
     }
     __syncthreads();
     const double2* __restrict__ Vp2 = reinterpret_cast<const double2*>(a.Vb);
