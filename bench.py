@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -255,7 +256,7 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int, path: str | None):
         self.proc = None
-        self.path = path or os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"phic_clocks_rank{gpu_index}_{os.getpid()}.csv")
         self.gpu_index = gpu_index
 
     def __enter__(self):
