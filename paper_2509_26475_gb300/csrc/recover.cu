@@ -1,124 +1,20 @@
-// Single-instance launches of Algorithm 3, recovery phase: one cooperative grid, the whole grid one team.
-#include "coop_launch.cuh"
+// Single-instance launches of Algorithm 3's recovery phase: dispatch on the storage precision to the
+// per-precision units (recover_f32.cu, recover_f64.cu).
+#include "kernels.h"
 
 namespace phic {
 
-extern __shared__ __align__(16) unsigned char recover_dyn_smem[];
-
-// The dynamic shared memory the block was launched with, for E (see recover_body).
-__device__ __forceinline__ unsigned dynamic_smem_bytes() {
-  unsigned b;
-  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(b));
-  return b;
-}
-
-template <typename T, int CW, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) recover_kernel(const SolveArgs a) {
-  __shared__ RecoverSmem<T> sm;
-  Team tm = grid_team(a.ctlR, a.spin_ns);
-  int phase = 0;
-  const unsigned eb = dynamic_smem_bytes();
-  recover_body<T, CW, false, true>(a, tm, sm, phase, 0x7fffffff, nullptr,
-                                   eb ? reinterpret_cast<T*>(recover_dyn_smem) : nullptr, eb);
-}
-
-// Low-rank operators: the same body with A applied as U (W^T x) (one team reduction per product).
-template <typename T, int CW>
-__global__ void __launch_bounds__(kBlock, 2) lr_recover_kernel(const SolveArgs a) {
-  __shared__ RecoverSmem<T> sm;
-  __shared__ LowRankSmem<T> lz;
-  Team tm = grid_team(a.ctlR, a.spin_ns);
-  int phase = 0;
-  recover_body<T, CW, true>(a, tm, sm, phase, 0x7fffffff, &lz);
-}
-
-namespace {
-
-// Keeping the recovery's E in shared memory (recover_body) takes two of the four tile passes of every
-// Taylor term off DRAM and L2.  The dynamic shared memory a launch of `kernel` at b blocks per SM
-// needs for one block's rows of E, if they fit next to its static shared memory; 0 otherwise.
-#ifndef PHIC_E_SMEM
-#define PHIC_E_SMEM 1
-#endif
-template <typename K>
-size_t e_smem_bytes(K kernel, const SolveArgs& a, size_t elem, int b) {
-  if (!PHIC_E_SMEM || b < 1) return 0;
-  int dev = 0, sms = 0, optin = 0, sm_total = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
-    return 0;
-  cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 0;
-  long long grid = (long long)sms * b;
-  const long long need = ((long long)a.n * a.F_lay.Lp2 + kBlock - 1) / kBlock;
-  if (need < grid) grid = need < 1 ? 1 : need;
-  const long long rows = (a.n + grid - 1) / grid;  // the most rows a team member owns
-  const size_t bytes = ((size_t)rows * a.F_lay.ws * elem + 15) / 16 * 16;
-  const size_t reserve = 1024;  // shared memory the hardware keeps per block
-  if (bytes > (size_t)optin || (size_t)b * (bytes + fa.sharedSizeBytes + reserve) > (size_t)sm_total) return 0;
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return 0;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBlock, bytes) != cudaSuccess || occ < b) return 0;
-  return bytes;
-}
-
-// Tiles up to 4 columns: the 2-block kernel.  Wider tiles: the wide_minb kernel with E in shared
-// memory if it fits at that residency, else the 2-block kernel (128 registers) at 2 blocks per SM with
-// E in shared memory if it fits there, else the wide_minb kernel with E in the workspace.
-template <typename T, int CW>
-cudaError_t launch_recover_cw(const SolveArgs& a, cudaStream_t st, int* g) {
-  constexpr int WB = wide_minb<T>();
-  const long long items = (long long)a.n * a.F_lay.Lp2;
-  const int cap = blocks_per_sm(sizeof(T));
-  auto k2 = recover_kernel<T, CW, 2>;
-  const int b2 = cap < 2 ? cap : 2;
-  if (a.F_lay.w <= 4) return coop_launch(k2, items, b2, a, st, g, 1 << 30, e_smem_bytes(k2, a, sizeof(T), b2));
-  auto kw = recover_kernel<T, CW, WB>;
-  const int bw = cap < WB ? cap : WB;
-  if (const size_t d = e_smem_bytes(kw, a, sizeof(T), bw)) return coop_launch(kw, items, bw, a, st, g, 1 << 30, d);
-  if (const size_t d = e_smem_bytes(k2, a, sizeof(T), b2)) return coop_launch(k2, items, b2, a, st, g, 1 << 30, d);
-  return coop_launch(kw, items, bw, a, st, g);
-}
-
-template <typename T>
-cudaError_t dispatch_recover(const SolveArgs& a, cudaStream_t st, int* g) {
-  switch (a.F_lay.cw) {
-    case 1: return launch_recover_cw<T, 1>(a, st, g);
-    case 2: return launch_recover_cw<T, 2>(a, st, g);
-#if PHIC_CW_MAX_F32 >= 8
-    case 8:
-      if constexpr (sizeof(T) == 4) return launch_recover_cw<T, 8>(a, st, g);
-      return cudaErrorInvalidValue;
-#endif
-    default: return launch_recover_cw<T, 4>(a, st, g);
-  }
-}
-}  // namespace
-
-template <typename T>
-cudaError_t dispatch_lr_recover(const SolveArgs& a, cudaStream_t st) {
-  const long long items = (long long)a.n * a.F_lay.Lp2;
-  const int bps = blocks_per_sm(sizeof(T)) < 2 ? blocks_per_sm(sizeof(T)) : 2;
-  switch (a.F_lay.cw) {
-    case 1: return coop_launch(lr_recover_kernel<T, 1>, items, bps, a, st, nullptr, kLowRankMaxGrid);
-    case 2: return coop_launch(lr_recover_kernel<T, 2>, items, bps, a, st, nullptr, kLowRankMaxGrid);
-#if PHIC_CW_MAX_F32 >= 8
-    case 8:
-      if constexpr (sizeof(T) == 4) return coop_launch(lr_recover_kernel<T, 8>, items, bps, a, st, nullptr, kLowRankMaxGrid);
-      return cudaErrorInvalidValue;
-#endif
-    default: return coop_launch(lr_recover_kernel<T, 4>, items, bps, a, st, nullptr, kLowRankMaxGrid);
-  }
-}
+cudaError_t launch_recover_f32(const SolveArgs& a, cudaStream_t st, int* grid_out);
+cudaError_t launch_recover_f64(const SolveArgs& a, cudaStream_t st, int* grid_out);
+cudaError_t launch_lr_recover_f32(const SolveArgs& a, cudaStream_t st);
+cudaError_t launch_lr_recover_f64(const SolveArgs& a, cudaStream_t st);
 
 cudaError_t launch_lr_recover(const SolveArgs& a, int prec, cudaStream_t st) {
-  return prec == PHIC_F32 ? dispatch_lr_recover<float>(a, st) : dispatch_lr_recover<double>(a, st);
+  return prec == PHIC_F32 ? launch_lr_recover_f32(a, st) : launch_lr_recover_f64(a, st);
 }
 
 cudaError_t launch_recover(const SolveArgs& a, int prec, cudaStream_t st, int* grid_out) {
-  return prec == PHIC_F32 ? dispatch_recover<float>(a, st, grid_out) : dispatch_recover<double>(a, st, grid_out);
+  return prec == PHIC_F32 ? launch_recover_f32(a, st, grid_out) : launch_recover_f64(a, st, grid_out);
 }
 
 }  // namespace phic
