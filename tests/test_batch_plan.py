@@ -139,3 +139,17 @@ def test_host_checks_reject_bad_items():
     arr[0].params = None
     assert lib.phic_batch_workspace_size(arr, 1, None, ctypes.byref(size)) == capi.PHIC_INVALID_ARG
     assert lib.phic_batch_workspace_size(arr, 0, None, ctypes.byref(size)) == capi.PHIC_INVALID_ARG
+
+
+def test_hints_steer_the_cost_model():
+    """s_hint sets an instance's outer steps ceil(s_hint max|t|): of two otherwise equal instances the one
+    with the larger hint is costed longer and placed first, and the estimated makespan grows with it."""
+    base = dict(n=50000, nnz=250000, p=3, t=[1e-3, 2e-3], prec=1)
+    small = dict(base, s_hint=500.0)    # one outer step
+    large = dict(base, s_hint=20000.0)  # 40 outer steps
+    team, lists, mk_mix, _ = _plan([small, large], 16, 4096)
+    firsts = [lst[0][0] for lst in lists if lst]
+    assert firsts.count(1) == team[1]  # the long instance heads the lists of all its members
+    _, _, mk_small, _ = _plan([small, dict(small)], 16, 4096)
+    _, _, mk_large, _ = _plan([large, dict(large)], 16, 4096)
+    assert mk_small < mk_mix < mk_large
