@@ -1,18 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark of the phi-combination solver on one GB300 (or N replicas under torchrun).
 
-Workload (expRK4s6-shaped block): 3-D 7-point first-order upwind convection-diffusion on a 64^3
-Dirichlet grid (n = 262,144, nnz = 1,810,432, Peclet 10, FP64 CSR), p = 3, r = 2,
-t = (h/2, h/3), alpha = (1/2, 1/3), h in {1e-4, 1e-2}, tol = 2^-53, v_j ~ N(0,1) (seed 2).
+Default workload (the precision configuration): 2-D first-order upwind advection-diffusion on a 1024 x 1024
+Dirichlet grid (n = 1,048,576, nnz = 5,238,784, Peclet 1e3, stiff and highly nonnormal), p = 4, r = 4,
+t = (1/4, 1/2, 3/4, 1) h, alpha = 1, h in {1e-5, 1e-4}, v_j ~ N(0,1) (seed 3), FP64 at tol = 2^-53.
 
-One step = Algorithm 1 (shift/scaling) on A + Algorithm 3 at h = 1e-4 + Algorithm 3 at h = 1e-2, so a
-step is 2 solves; value = solves/s over all ranks.  Inputs are resident in HBM before the timed
-region; L2 is flushed (a 2 x L2 write) between timed steps, outside the per-step CUDA events.
+One step = Algorithm 1 (shift/scaling) on A + Algorithm 3 at h = 1e-5 + Algorithm 3 at h = 1e-4, so a step
+is 2 solves; value = solves/s over all ranks.  Inputs are resident in HBM before the timed region; L2 is
+flushed (a 2 x L2 write) between timed steps, outside the per-step CUDA events (the working set, about
+1.4 GB, exceeds L2 anyway).  The line also carries:
+  * ``roofline`` of the dominant kernel (the recovery at h = 1e-4) against the FP64 FMA rate measured by the
+    library's probe kernel just before the timed region, with its HBM view;
+  * ``kernels``: every kernel's share of the step, and Algorithm 1's kernel against HBM;
+  * ``fp32``: the same step at tol 2^-24 with FP32 storage (its own value, HBM roofline and errors);
+  * ``e2e`` through the public API from pinned host buffers;
+  * ``cpu_baseline``: the FP64 C oracle on the host cores (Algorithm 1 + Algorithm 3 at h = 1e-5), whose
+    result also gives the errors of both precisions at h = 1e-5.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                    [--workload NAME] [--precision f64|f32|mixed] [--sweep]
 
-``--impl reference`` times the CPU oracle (plain FP64 C, OpenMP over sparse-product rows) on the same
-workload on this machine's host cores.
+``--sweep`` runs the 1024^2 workload at h = 1e-5 .. 1e-1 in both precisions (one solve each) and prints one
+JSON line per (precision, h).  ``--impl reference`` times the CPU oracle (plain FP64 C, OpenMP over
+sparse-product rows) on a bounded sample of the same workload on this machine's host cores.
 """
 from __future__ import annotations
 
@@ -31,22 +41,30 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "φ-comb solves/s & SpMM HBM GB/s (% peak) at stated tol; p50/p99 serve latency"
-# FP64 pipe of a GB300 SM: 2 FMA/clk (1.91 measured), 152 SMs, 2070 MHz maximum SM clock; 2 flops an FMA.
-FP64_PEAK_GFLOPS = 2.0 * 2.0 * 152 * 2.070
+SMS = 152  # streaming multiprocessors of a GB300
+# FP64 pipe of a GB300 SM by its unit count: 2 FMA/clk, 152 SMs, 2070 MHz maximum SM clock; 2 flops an FMA.
+# Context only: the roofline divides by the rate the probe kernel measures.
+FP64_DERIVED_GFLOPS = 2.0 * 2.0 * SMS * 2.070
 
-# Workload of the benchmark line (defaults) and the auxiliary FP32/FP64 precision workload.
+# Single-operator workloads: the default (advdiff2d-1024) and the expRK4s6-shaped 64^3 block.
 WORKLOADS = {
-    "convdiff3d-64": dict(hs=(1e-4, 1e-2), p=3, r=2, t=lambda h: [h / 2.0, h / 3.0],
-                          name="convdiff3d-64^3 Pe10 (n=262144) p=3 r=2 t=(h/2,h/3) alpha=(1/2,1/3) h={1e-4,1e-2}"),
     "advdiff2d-1024": dict(hs=(1e-5, 1e-4), p=4, r=4, t=lambda h: [0.25 * h, 0.5 * h, 0.75 * h, h],
                            name="advdiff2d-1024^2 Pe1e3 (n=1048576) p=4 r=4 t=(1/4,1/2,3/4,1)h alpha=1 h={1e-5,1e-4}"),
+    "convdiff3d-64": dict(hs=(1e-4, 1e-2), p=3, r=2, t=lambda h: [h / 2.0, h / 3.0],
+                          name="convdiff3d-64^3 Pe10 (n=262144) p=3 r=2 t=(h/2,h/3) alpha=(1/2,1/3) h={1e-4,1e-2}"),
 }
-WORKLOAD = "convdiff3d-64"
+SWEEP_HS = (1e-5, 1e-4, 1e-3, 1e-2, 1e-1)
+SERVE_CURVE_RATES = (100.0, 200.0, 400.0, 700.0, 1000.0, 1500.0)
+WORKLOAD = "advdiff2d-1024"
 PRECISION = "f64"
 HS = WORKLOADS[WORKLOAD]["hs"]
 TOL = 2.0**-53
-P, R = 3, 2
-WORKLOAD_NAME = WORKLOADS[WORKLOAD]["name"] + " tol=2^-53"
+P, R = 4, 4
+WORKLOAD_NAME = WORKLOADS[WORKLOAD]["name"] + " tol=2^-53 FP64"
+
+
+def tol_of(precision: str) -> float:
+    return 2.0**-53 if precision == "f64" else 2.0**-24
 
 
 def configure(workload_name: str, precision: str):
@@ -60,19 +78,25 @@ def configure(workload_name: str, precision: str):
     cfg = WORKLOADS[workload_name]
     WORKLOAD, PRECISION = workload_name, precision
     HS, P, R = cfg["hs"], cfg["p"], cfg["r"]
-    TOL = 2.0**-53 if precision == "f64" else 2.0**-24
-    WORKLOAD_NAME = cfg["name"] + (" tol=2^-53 FP64" if precision == "f64" else " tol=2^-24 FP32")
+    TOL = tol_of(precision)
+    WORKLOAD_NAME = workload_label(precision)
+
+
+def workload_label(precision: str) -> str:
+    return WORKLOADS[WORKLOAD]["name"] + (" tol=2^-53 FP64" if precision == "f64" else " tol=2^-24 FP32")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="convdiff3d-64",
+    ap.add_argument("--no-companion", action="store_true", help="skip the FP32 companion of the default line")
+    ap.add_argument("--sweep", action="store_true", help="advdiff2d-1024: h = 1e-5 .. 1e-1 in FP64 and FP32")
+    ap.add_argument("--workload", default="advdiff2d-1024",
                     choices=sorted(WORKLOADS) + ["batch512", "serve", "exprk-adr", "lowrank-m2"])
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "mixed"])
     ap.add_argument("--requests", type=int, default=1000, help="serve: number of arrivals")
@@ -145,21 +169,25 @@ def t_of(h):
     return WORKLOADS[WORKLOAD]["t"](h)
 
 
-def torch_dtype():
+def torch_dtype(precision: str | None = None):
     import torch
 
-    return torch.float64 if PRECISION == "f64" else torch.float32
+    return torch.float64 if (precision or PRECISION) == "f64" else torch.float32
 
 
-def recorded_traffic(terms: int):
+TRAFFIC_RECORDS = {("convdiff3d-64", "f64"): "recover_kernel_convdiff3d_64.json",
+                   ("advdiff2d-1024", "f32"): "recover_kernel_advdiff2d_1024_fp32.json",
+                   ("advdiff2d-1024", "f64"): "recover_kernel_advdiff2d_1024_fp64.json"}
+
+
+def recorded_traffic(terms: int, precision: str | None = None):
     """DRAM bytes of one launch of the dominant kernel from the committed ncu record of this workload and
     precision, if that record was taken on the current kernel sources (sha256 of each); None otherwise.
     A record of a shorter launch of the same kernel (fewer Taylor terms) is scaled by the terms: every
     term moves the same bytes once the working set exceeds L2, which is when the scaling is used."""
     import hashlib
 
-    name = "recover_kernel_convdiff3d_64.json" if (WORKLOAD, PRECISION) == ("convdiff3d-64", "f64") else \
-        "recover_kernel_advdiff2d_1024_fp32.json" if (WORKLOAD, PRECISION) == ("advdiff2d-1024", "f32") else None
+    name = TRAFFIC_RECORDS.get((WORKLOAD, precision or PRECISION))
     if name is None:
         return None
     try:
@@ -191,30 +219,47 @@ def solves_per_second(ms_per_step: float, world: int) -> float:
     return world * len(HS) / (ms_per_step / 1000.0)
 
 
+def rel_errors(W, ref):
+    """Relative 2-norm error of each combination w_i (rows of W) against ref."""
+    import numpy as np
+
+    W = np.asarray(W, dtype=np.float64)
+    return [float(np.linalg.norm(W[i] - ref[i]) / np.linalg.norm(ref[i])) for i in range(ref.shape[0])]
+
+
 # ------------------------------------------------------------------------------------------------
 # Oracle timing (CPU)
 # ------------------------------------------------------------------------------------------------
-def oracle_step(oracle, A, V, alpha):
-    sel = oracle.select(A)
-    for h in HS:
-        oracle.solve(A, V, t_of(h), alpha, TOL, sel["s"], sel["xi"])
+def oracle_sample_hs():
+    """The solves of a step the oracle runs as its sample: the whole step on the 64^3 workload (about 3 s
+    on 16 Grace cores); on the 1024^2 workload only h = 1e-5 (about 20 s with Algorithm 1), since the
+    h = 1e-4 solve takes about 9 times the recovery work."""
+    return tuple(HS) if WORKLOAD == "convdiff3d-64" else (HS[0],)
 
 
-def time_oracle(steps, warmup):
+def oracle_sample_text(hs) -> str:
+    if len(hs) == len(HS):
+        return ("Algorithm 1 + Algorithm 3 at h = " + " and ".join(f"{h:g}" for h in hs) +
+                ": one full step of the workload, FP64 C oracle, OpenMP over sparse-product rows")
+    return (f"Algorithm 1 + Algorithm 3 at h = {hs[0]:g} only (one of the step's {len(HS)} solves, the cheaper: "
+            f"h = {HS[-1]:g} has about 9 times its recovery terms), FP64 C oracle, OpenMP over sparse-product "
+            "rows; value = solves of the sample / its time, so it overstates the oracle's rate on the full step")
+
+
+def time_oracle_sample(A, V, alpha):
+    """One run of the oracle's sample: Algorithm 1 (its own xi, s), then Algorithm 3 at each sampled h.
+    Returns (seconds, {h: W}, threads, selection)."""
     import oracle
 
     oracle.build()
-    cores = os.cpu_count() or 1
-    used = oracle.set_threads(cores)
-    A, V, alpha = workload()
-    for _ in range(warmup):
-        oracle_step(oracle, A, V, alpha)
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        oracle_step(oracle, A, V, alpha)
-        times.append(time.perf_counter() - t0)
-    return times, used
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    hs = oracle_sample_hs()
+    t0 = time.perf_counter()
+    sel = oracle.select(A)
+    out = {}
+    for h in hs:
+        out[h], _ = oracle.solve(A, V, t_of(h), alpha, 2.0**-53, sel["s"], sel["xi"])
+    return time.perf_counter() - t0, out, cores, sel
 
 
 def run_reference(args, rank, world):
@@ -229,17 +274,26 @@ def run_reference(args, rank, world):
                           "form of the 400,000-row low-rank operator (1.3 TB) does not fit"}), flush=True)
         return 0
     steps, warmup = max(1, args.steps), max(0, args.warmup)
-    # bound the whole run to a few minutes: at most 6 timed steps and 1 warm-up of the full oracle step
-    steps_run, warm_run = min(steps, 6), min(warmup, 1)
-    times, cores = time_oracle(steps_run, warm_run)
+    # bound the whole run to a few minutes: each step is the oracle's sample of the workload
+    cap = 6 if WORKLOAD == "convdiff3d-64" else 3
+    steps_run, warm_run = min(steps, cap), min(warmup, 1 if WORKLOAD == "convdiff3d-64" else 0)
+    A, V, alpha = workload()
+    hs = oracle_sample_hs()
+    for _ in range(warm_run):
+        time_oracle_sample(A, V, alpha)
+    times = []
+    cores = 0
+    for _ in range(steps_run):
+        sec, _, cores, _ = time_oracle_sample(A, V, alpha)
+        times.append(sec)
     ms = 1000.0 * statistics.mean(times)
-    value = len(HS) / (ms / 1000.0)
-    sample = (f"full step (Algorithm 1 + Algorithm 3 at h=1e-4 and h=1e-2) on the benchmark workload; "
-              f"{steps_run} timed step(s) after {warm_run} warm-up (asked {steps}/{warmup})")
+    value = len(hs) / (ms / 1000.0)
+    sample = oracle_sample_text(hs) + f"; {steps_run} timed step(s) after {warm_run} warm-up (asked {steps}/{warmup})"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": steps_run, "warmup": warm_run, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "device": "host CPU", "threads": cores},
+            "config": {"workload": workload_label("f64"), "device": "host CPU", "threads": cores,
+                       "solves_per_step": len(hs)},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -317,6 +371,200 @@ def recover_kernel_work(n, nnz, wf, p, r, terms, outer_steps, b=8):
     return flops, bytes_
 
 
+def select_kernel_bytes(n, nnz, m, r_guard, evals, b=8):
+    """Algorithmic bytes of one Algorithm 1 launch: m sparse matrix-vector products (the guarded chain to
+    r and the extension to m), each reading the operator ((4 + b) nnz + 4(n+1)) and one basis vector and
+    writing the next (16 n); the rescaling V_j <- V_j / s0^j (16 n r); and one pass over the basis V_0..V_m
+    per objective evaluation ((m+1) 8 n)."""
+    spmv = (4 + b) * nnz + 4 * (n + 1) + 16 * n
+    return m * spmv + 16 * n * r_guard + evals * (m + 1) * 8 * n
+
+
+def measure_fp64_roof(lib, capi, dev, local_rank):
+    """FP64 FMA throughput of this GPU: the library's probe kernel (8 independent FMA chains per thread,
+    4 blocks of 256 threads per SM, no memory traffic), timed with CUDA events on the stream it runs on,
+    median of 8 launches of about 50 ms, SM clocks sampled meanwhile."""
+    import ctypes
+
+    import torch
+
+    stream = torch.cuda.current_stream(dev)
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    fmas = ctypes.c_int64(0)
+
+    def timed(iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        capi.check(lib.phic_probe_fp64_fma(int(iters), sink.data_ptr(), ctypes.byref(fmas), stream.cuda_stream),
+                   "phic_probe_fp64_fma")
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    timed(2000)
+    ms = timed(20000)
+    iters = max(1000, int(20000 * 50.0 / max(ms, 1e-3)))
+    with ClockSampler(local_rank, None) as clk:
+        times = [timed(iters) for _ in range(8)]
+    t = statistics.median(times) / 1000.0
+    gflops = 2.0 * fmas.value / t / 1e9
+    cs = clk.summary() or {}
+    mhz = cs.get("sm_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return {"gflops": gflops, "fma_per_clk_per_sm": fmas.value / t / (sms * mhz * 1e6), "sm_mhz": mhz,
+            "launch_ms": 1000.0 * t, "fmas_per_launch": int(fmas.value), "clocks": cs,
+            "derived_gflops": 2.0 * 2.0 * sms * (cs.get("sm_max_mhz") or 2070.0) / 1000.0,
+            "how": "phic_probe_fp64_fma: 8 independent FMA chains per thread, 4 x 256 threads per SM, median "
+                   "of 8 launches, CUDA events"}
+
+
+class SingleRun:
+    """Algorithm 1 + Algorithm 3 at each h of the workload, in one precision, on resident inputs: the
+    step of the benchmark line.  Events between the phases give every kernel's time."""
+
+    def __init__(self, api, capi, precision, dev, A_h, V_h, alpha):
+        import torch
+
+        self.api, self.capi, self.precision, self.dev = api, capi, precision, dev
+        self.tol = tol_of(precision)
+        self.alpha = alpha
+        dt = torch_dtype(precision)
+        self.prec = capi.PHIC_F64 if precision == "f64" else capi.PHIC_F32
+        self.A = api.DeviceCSR.from_host(A_h, device=dev, dtype=dt)
+        self.V = torch.as_tensor(V_h).to(dt).to(dev)
+        n, nnz = self.A.n, self.A.nnz
+        self.params = api.new_params(dev)
+        self.stats = [api.new_stats(dev) for _ in HS]
+        self.W = [torch.empty((R, n), dtype=dt, device=dev) for _ in HS]
+        self.ws_sel = torch.empty(api.select_workspace_bytes(n), dtype=torch.uint8, device=dev)
+        self.ws_sol = torch.empty(api.solve_workspace_bytes(n, nnz, P, R, self.prec), dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.current_stream(dev)
+
+    def step(self, evs=None):
+        """evs: None or 1 + 2 len(HS) events, recorded after select and after each series and recovery."""
+        api, capi = self.api, self.capi
+        api.select_params(self.A, tol=self.tol, out=self.params, workspace=self.ws_sel)
+        if evs is not None:
+            evs[0].record(self.stream)
+        for idx, h in enumerate(HS):
+            for ph, flag in enumerate((capi.PHIC_PHASE_SERIES, capi.PHIC_PHASE_RECOVER)):
+                api.solve(self.A, self.V, t_of(h), self.alpha, self.tol, self.params, out=self.W[idx],
+                          stats=self.stats[idx], workspace=self.ws_sol, flags=flag)
+                if evs is not None:
+                    evs[1 + 2 * idx + ph].record(self.stream)
+
+    def check_status(self):
+        import torch
+
+        torch.cuda.synchronize(self.dev)
+        self.capi.check(self.api.read_params(self.params)["status"], "select (device)")
+        for st in self.stats:
+            self.capi.check(self.api.read_stats(st)["status"], "solve (device)")
+
+    def timed(self, K, warmup, lib, local_rank, dist):
+        """W warm-up steps, then K steps each bracketed by CUDA events (per phase), an L2 flush (2 x L2
+        write) before each step outside its events; barrier + synchronize on both sides."""
+        import torch
+
+        for _ in range(max(warmup, 0)):
+            self.step()
+        self.check_status()
+        l2 = torch.cuda.get_device_properties(self.dev).L2_cache_size
+        flush = torch.empty(2 * l2, dtype=torch.uint8, device=self.dev)
+        nph = 1 + 2 * len(HS)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        evp = [[torch.cuda.Event(enable_timing=True) for _ in range(nph)] for _ in range(K)]
+        launches0 = lib.phic_launch_count()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(self.dev)
+        wall0 = time.perf_counter()
+        with ClockSampler(local_rank, None) as clk:
+            for k in range(K):
+                flush.fill_(k & 0xFF)
+                ev0[k].record(self.stream)
+                self.step(evp[k])
+            torch.cuda.synchronize(self.dev)
+        wall = time.perf_counter() - wall0
+        if dist is not None:
+            dist.barrier()
+        self.launches = lib.phic_launch_count() - launches0
+        self.check_status()
+        self.wall = wall
+        self.clocks = clk.summary()
+        self.step_ms = [ev0[k].elapsed_time(evp[k][-1]) for k in range(K)]
+        phase_ms = []
+        for k in range(K):
+            prev = ev0[k]
+            row = []
+            for e in evp[k]:
+                row.append(prev.elapsed_time(e))
+                prev = e
+            phase_ms.append(row)
+        self.phase_ms = [statistics.mean(col) for col in zip(*phase_ms)]
+        self.sts = [self.api.read_stats(s) for s in self.stats]
+        self.prm = self.api.read_params(self.params)
+        return statistics.mean(self.step_ms)
+
+    def kernels(self, hbm_peak):
+        """Per-kernel time in the step and share; Algorithm 1's kernel against HBM."""
+        n, nnz = self.A.n, self.A.nnz
+        out = {"select_kernel": {"ms": self.phase_ms[0]}}
+        for idx, h in enumerate(HS):
+            out[f"series_kernel h={h:g}"] = {"ms": self.phase_ms[1 + 2 * idx],
+                                             "terms": self.sts[idx]["series_terms"]}
+            out[f"recover_kernel h={h:g}"] = {"ms": self.phase_ms[2 + 2 * idx],
+                                              "terms": self.sts[idx]["recovery_terms"],
+                                              "us_per_term": 1000.0 * self.phase_ms[2 + 2 * idx] /
+                                              max(1, self.sts[idx]["recovery_terms"])}
+        tot = sum(v["ms"] for v in out.values())
+        for v in out.values():
+            v["share"] = v["ms"] / tot if tot > 0 else None
+        b = 8 if self.precision == "f64" else 4
+        sb = select_kernel_bytes(n, nnz, 61, self.prm["r"], self.prm["evals"], b)
+        gbs = sb / (self.phase_ms[0] / 1000.0) / 1e9
+        out["select_kernel"].update({"evals": self.prm["evals"], "r": self.prm["r"], "bytes": sb,
+                                     "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                                     "bytes_note": "m products ((4+b) nnz + 4(n+1) + 16n each), the rescaling "
+                                                   "(16 n r) and one pass over V_0..V_m per objective "
+                                                   "evaluation ((m+1) 8 n); of measured HBM"})
+        return out
+
+    def roofline(self, roof, hbm_peak):
+        """The dominant kernel: the recovery at the largest h."""
+        n, nnz = self.A.n, self.A.nnz
+        st = self.sts[-1]
+        b = 8 if self.precision == "f64" else 4
+        flops, bytes_ = recover_kernel_work(n, nnz, 2 * R, P, R, st["recovery_terms"], st["s_int"] - 1, b)
+        rec_s = self.phase_ms[-1] / 1000.0
+        achieved = flops / rec_s / 1e9
+        hbm_gbs = bytes_ / rec_s / 1e9
+        kernel = f"recover_kernel (Algorithm 3 recovery loop, h={HS[-1]:g})"
+        common = {"kernel": kernel, "traffic": recorded_traffic(st["recovery_terms"], self.precision),
+                  "launch_ms": self.phase_ms[-1], "terms_per_launch": st["recovery_terms"],
+                  "bytes_per_launch": bytes_, "flops_per_launch": flops}
+        if self.precision == "f64" and roof is not None:
+            return {"bound": "alu", "achieved": achieved, "peak": roof["gflops"], "unit": "FP64 GFLOP/s",
+                    "frac": achieved / roof["gflops"], **common,
+                    "peak_note": f"of measured: FP64 FMA rate of the probe kernel before the timed region "
+                                 f"({roof['fma_per_clk_per_sm']:.3f} FMA/clk/SM at {roof['sm_mhz']:.0f} MHz); "
+                                 "achieved counts (2 nnz + 3 n) 2r flops per Taylor term",
+                    "peak_derived": roof["derived_gflops"], "frac_of_derived": achieved / roof["derived_gflops"],
+                    "hbm_view": {"algorithmic_gbs": hbm_gbs, "peak_gbs": hbm_peak,
+                                 "frac_of_measured": hbm_gbs / hbm_peak}}
+        return {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+                **common, "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured); algorithmic bytes "
+                                       "(4+b) nnz + 4(n+1) + 4 n 2r b per Taylor term"}
+
+    def summary(self):
+        return {"s": self.prm["s"], "xi": self.prm["xi"], "s_int": [x["s_int"] for x in self.sts],
+                "terms": [x["series_terms"] + x["recovery_terms"] for x in self.sts]}
+
+    def release(self):
+        for name in ("A", "V", "W", "ws_sel", "ws_sol", "params", "stats"):
+            setattr(self, name, None)
+
+
 def main():
     args = parse()
     rank, world, local_rank = dist_env()
@@ -335,6 +583,12 @@ def main():
         return run_exprk(args, rank, world, local_rank)
     if WORKLOAD == "lowrank-m2":
         return run_lowrank(args, rank, world, local_rank)
+    if args.sweep:
+        return run_sweep(args, rank, world, local_rank)
+    return run_single(args, rank, world, local_rank)
+
+
+def run_single(args, rank, world, local_rank):
     import numpy as np
     import torch
 
@@ -349,124 +603,61 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
+    hbm_peak = float(_peaks().get("hbm_gbs", 6800.0))
+    roof = measure_fp64_roof(lib, capi, dev, local_rank)
 
     A_h, V_h, alpha = workload()
-    dt = torch_dtype()
-    prec = capi.PHIC_F64 if PRECISION == "f64" else capi.PHIC_F32
-    A = api.DeviceCSR.from_host(A_h, device=dev, dtype=dt)
-    V = torch.as_tensor(V_h).to(dt).to(dev)
-    n, nnz = A.n, A.nnz
-    params = api.new_params(dev)
-    stats = [api.new_stats(dev) for _ in HS]
-    W = [torch.empty((R, n), dtype=dt, device=dev) for _ in HS]
-    ws_sel = torch.empty(api.select_workspace_bytes(n), dtype=torch.uint8, device=dev)
-    ws_sol = torch.empty(api.solve_workspace_bytes(n, nnz, P, R, prec), dtype=torch.uint8, device=dev)
-    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-    flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def step(ev_rec=None):
-        api.select_params(A, tol=TOL, out=params, workspace=ws_sel)
-        for idx, h in enumerate(HS):
-            if ev_rec is not None and idx == len(HS) - 1:
-                api.solve(A, V, t_of(h), alpha, TOL, params, out=W[idx], stats=stats[idx], workspace=ws_sol,
-                          flags=capi.PHIC_PHASE_SERIES)
-                ev_rec[0].record(stream)
-                api.solve(A, V, t_of(h), alpha, TOL, params, out=W[idx], stats=stats[idx], workspace=ws_sol,
-                          flags=capi.PHIC_PHASE_RECOVER)
-                ev_rec[1].record(stream)
-            else:
-                api.solve(A, V, t_of(h), alpha, TOL, params, out=W[idx], stats=stats[idx], workspace=ws_sol)
-
-    def check_status():
-        torch.cuda.synchronize(dev)
-        capi.check(api.read_params(params)["status"], "select (device)")
-        for st in stats:
-            capi.check(api.read_stats(st)["status"], "solve (device)")
-
-    for _ in range(max(args.warmup, 0)):
-        step()
-    check_status()
-
     K = max(1, args.steps)
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    launches0 = lib.phic_launch_count()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    wall0 = time.perf_counter()
-    with ClockSampler(local_rank, None) as clk:
-        for k in range(K):
-            flush.fill_(k & 0xFF)  # 2 x L2 write between steps, outside the step's events
-            ev0[k].record(stream)
-            step(evr[k])
-            ev1[k].record(stream)
-        torch.cuda.synchronize(dev)
-    wall = time.perf_counter() - wall0
-    if dist is not None:
-        dist.barrier()
-    launches = lib.phic_launch_count() - launches0
-    check_status()
-    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(K)]
-    rec_ms = [evr[k][0].elapsed_time(evr[k][1]) for k in range(K)]
-    ms = reduce_max_over_ranks(statistics.mean(step_ms), dist, dev)
+    run = SingleRun(api, capi, PRECISION, dev, A_h, V_h, alpha)
+    ms = reduce_max_over_ranks(run.timed(K, args.warmup, lib, local_rank, dist), dist, dev)
     value = solves_per_second(ms, world)
-
-    st_last = api.read_stats(stats[-1])
-    prm = api.read_params(params)
-    wf = 2 * R
-    b = 8 if PRECISION == "f64" else 4
-    flops, bytes_ = recover_kernel_work(n, nnz, wf, P, R, st_last["recovery_terms"], st_last["s_int"] - 1, b)
-    rec_s = statistics.mean(rec_ms) / 1000.0
-    achieved = flops / rec_s / 1e9
-    hbm_gbs = bytes_ / rec_s / 1e9
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    kernel = f"recover_kernel (Algorithm 3 recovery loop, h={HS[-1]:g})"
-    if PRECISION == "f64":
-        roofline = {"bound": "alu", "kernel": kernel,
-                    "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "FP64 GFLOP/s",
-                    "frac": achieved / FP64_PEAK_GFLOPS,
-                    "traffic": recorded_traffic(st_last["recovery_terms"]),
-                    "peak_note": "FP64 pipe: 2 FMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (probe measured "
-                                 "1.91 FMA/clk/SM); achieved counts (2 nnz + 3 n) 2r flops per Taylor term",
-                    "launch_ms": statistics.mean(rec_ms), "terms_per_launch": st_last["recovery_terms"],
-                    "hbm_view": {"algorithmic_gbs": hbm_gbs, "peak_gbs": hbm_peak,
-                                 "frac_of_measured": hbm_gbs / hbm_peak}}
-    else:
-        roofline = {"bound": "hbm", "kernel": kernel, "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_gbs / hbm_peak, "traffic": recorded_traffic(st_last["recovery_terms"]),
-                    "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured)",
-                    "launch_ms": statistics.mean(rec_ms), "terms_per_launch": st_last["recovery_terms"]}
-
+    n, nnz = run.A.n, run.A.nnz
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": PRECISION, "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "n": n, "nnz": nnz, "p": P, "r": R, "h": list(HS),
                        "tol": "2^-53" if PRECISION == "f64" else "2^-24",
                        "step": "Algorithm 1 + Algorithm 3 at each h (2 solves)",
-                       "l2": "flushed between steps (2 x L2 write, outside the step events)",
-                       "parallelism": f"replicas x{world}",
-                       "s": prm["s"], "xi": prm["xi"], "s_int": [api.read_stats(s)["s_int"] for s in stats],
-                       "terms": [api.read_stats(s)["series_terms"] + api.read_stats(s)["recovery_terms"] for s in stats]},
-            "roofline": roofline, "gpu_launches": int(launches), "wall_s_timed_region": wall}
-    clk_sum = clk.summary()
-    if clk_sum:
-        line["clocks"] = clk_sum
+                       "l2": "flushed between steps (2 x L2 write, outside the step events); working set above L2",
+                       "parallelism": f"replicas x{world}", **run.summary()},
+            "roofline": run.roofline(roof, hbm_peak), "kernels": run.kernels(hbm_peak),
+            "fp64_roof": roof, "gpu_launches": int(run.launches), "wall_s_timed_region": run.wall}
+    if run.clocks:
+        line["clocks"] = run.clocks
+    W_primary = [w.double().cpu().numpy() for w in run.W]
+    run.release()
+    torch.cuda.empty_cache()
+
+    # FP32 companion: the same step at tol 2^-24 with FP32 storage
+    comp = None
+    if WORKLOAD == "advdiff2d-1024" and PRECISION == "f64" and not args.no_companion:
+        c32 = SingleRun(api, capi, "f32", dev, A_h, V_h, alpha)
+        ms32 = reduce_max_over_ranks(c32.timed(K, args.warmup, lib, local_rank, dist), dist, dev)
+        W32 = [w.double().cpu().numpy() for w in c32.W]
+        comp = {"value": solves_per_second(ms32, world), "unit": "solves/s", "ms_per_step": ms32, "dtype": "f32",
+                "tol": "2^-24", "workload": workload_label("f32"), **c32.summary(),
+                "roofline": c32.roofline(None, hbm_peak), "kernels": c32.kernels(hbm_peak),
+                "gpu_launches": int(c32.launches), "clocks": c32.clocks,
+                "errors": {f"h={HS[-1]:g} vs GPU FP64 (same step)": max(rel_errors(W32[-1], W_primary[-1]))}}
+        line["fp32"] = comp
+        c32.release()
+        torch.cuda.empty_cache()
 
     if not args.no_e2e:
-        line["e2e"] = e2e(api, capi, A_h, V_h, alpha, dev, stream, K, world, dist)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD == "convdiff3d-64":
-        times, cores = time_oracle(1, 0)
-        line["cpu_baseline"] = {"value": len(HS) / times[0], "unit": "solves/s", "cores": cores, "kind": "oracle",
-                                "sample": "one full step (Algorithm 1 + Algorithm 3 at h=1e-4 and 1e-2) of the "
-                                          "benchmark workload, FP64 C oracle, OpenMP over sparse-product rows"}
+        line["e2e"] = e2e(api, capi, A_h, V_h, alpha, dev, torch.cuda.current_stream(dev), K, world, dist)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sec, ref, cores, sel = time_oracle_sample(A_h, V_h, alpha)
+        hs = oracle_sample_hs()
+        line["cpu_baseline"] = {"value": len(hs) / sec, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                "sample": oracle_sample_text(hs), "seconds": sec}
+        errs = {}
+        for idx, h in enumerate(HS):
+            if h in ref:
+                errs[f"h={h:g} vs FP64 oracle"] = max(rel_errors(W_primary[idx], ref[h]))
+                if comp is not None:
+                    comp["errors"][f"h={h:g} vs FP64 oracle"] = max(rel_errors(W32[idx], ref[h]))
+        line["errors"] = {"metric": "max over i of ||w_i - w_i_ref||_2 / ||w_i_ref||_2", **errs,
+                          "oracle_s": sel["s"], "oracle_xi": sel["xi"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -477,7 +668,6 @@ def main():
 def e2e(api, capi, A_h, V_h, alpha, dev, stream, K, world, dist):
     """Same step through the public API from pinned host buffers: copy A and V in, Algorithm 1, both
     solves, copy the results out; CUDA events around everything."""
-    import numpy as np
     import torch
 
     dt = torch_dtype()
@@ -512,6 +702,98 @@ def e2e(api, capi, A_h, V_h, alpha, dev, stream, K, world, dist):
     ms = reduce_max_over_ranks(e0.elapsed_time(e1) / K, dist, dev)
     return {"value": solves_per_second(ms, world), "unit": "solves/s", "ms_per_step": ms,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def golden_samples(h: float):
+    """The oracle's sampled answer at step h for the 1024^2 workload (tests/golden/advdiff2d_1024_h<h>.json,
+    written by tests/golden/make_advdiff2d_1024.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"advdiff2d_1024_h{h:g}.json")
+    return json.load(open(path)) if os.path.exists(path) else None
+
+
+def sampled_error(W, gold) -> float:
+    """Largest relative 2-norm error over the combinations, on the oracle's sampled entries."""
+    import numpy as np
+
+    idx = np.asarray(gold["index"], dtype=np.int64)
+    errs = []
+    for i in range(len(gold["values"])):
+        ref = np.asarray(gold["values"][i])
+        errs.append(float(np.linalg.norm(np.asarray(W[i], dtype=np.float64)[idx] - ref) / np.linalg.norm(ref)))
+    return max(errs)
+
+
+def run_sweep(args, rank, world, local_rank):
+    """advdiff2d-1024 at h = 1e-5 .. 1e-1 in FP64 (tol 2^-53) and FP32 (tol 2^-24): Algorithm 1 once per
+    precision, then one solve per h (a warm-up solve first where it is short), CUDA events around the
+    series and the recovery.  Errors: against the FP64 oracle's sampled answer where tests/golden holds it
+    (h <= 1e-3), else the FP32 result against the GPU FP64 result at the same h (stated as such).  One JSON
+    line per (precision, h), then a summary line."""
+    import numpy as np
+    import torch
+
+    from paper_2509_26475_gb300 import api, build, capi
+
+    if WORKLOAD != "advdiff2d-1024" or world > 1:
+        raise SystemExit("--sweep runs the advdiff2d-1024 workload on one GPU")
+    build.build()
+    lib = capi.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    A_h, V_h, alpha = workload()
+    rows, W64 = [], {}
+    for precision in ("f64", "f32"):
+        dt = torch_dtype(precision)
+        tol = tol_of(precision)
+        A = api.DeviceCSR.from_host(A_h, device=dev, dtype=dt)
+        V = torch.as_tensor(V_h).to(dt).to(dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        Pm = api.select_params(A, tol=tol, check=True)
+        e[1].record(stream)
+        torch.cuda.synchronize(dev)
+        sel_ms = e[0].elapsed_time(e[1])
+        prm = api.read_params(Pm)
+        for h in SWEEP_HS:
+            if h <= 1e-3:
+                api.solve(A, V, t_of(h), alpha, tol, Pm, check=True)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            with ClockSampler(local_rank, None) as clk:
+                ev[0].record(stream)
+                W, st = api.solve(A, V, t_of(h), alpha, tol, Pm, flags=capi.PHIC_PHASE_SERIES)
+                ev[1].record(stream)
+                api.solve(A, V, t_of(h), alpha, tol, Pm, out=W, stats=st, flags=capi.PHIC_PHASE_RECOVER)
+                ev[2].record(stream)
+                torch.cuda.synchronize(dev)
+            s = api.read_stats(st)
+            Wh = W.double().cpu().numpy()
+            gold = golden_samples(h)
+            if gold is not None:
+                err, against = sampled_error(Wh, gold), (f"FP64 oracle ({len(gold['index'])} sampled rows per "
+                                                         f"w_i; oracle solve {gold['oracle_seconds']['solve']:.0f} s "
+                                                         f"on {gold['oracle_host']})")
+            elif precision == "f32" and h in W64:
+                err, against = max(rel_errors(Wh, W64[h])), "GPU FP64 at the same h (no oracle run: too long)"
+            else:
+                err, against = None, "none (no oracle run at this h: too long on the host)"
+            if precision == "f64":
+                W64[h] = Wh
+            row = {"sweep": "advdiff2d-1024", "precision": precision, "tol": "2^-53" if precision == "f64" else "2^-24",
+                   "h": h, "status": s["status"], "s": s["s"], "xi": s["xi"], "s_int": s["s_int"],
+                   "series_terms": s["series_terms"], "recovery_terms": s["recovery_terms"],
+                   "series_ms": ev[0].elapsed_time(ev[1]), "recover_ms": ev[1].elapsed_time(ev[2]),
+                   "select_ms": sel_ms, "select_s": prm["s"], "max_rel_err": err, "error_against": against,
+                   "bar": 1e-12 if precision == "f64" else 5e-6,
+                   "meets_bar": None if err is None else bool(err <= (1e-12 if precision == "f64" else 5e-6)),
+                   "clocks": clk.summary()}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+        del A, V, Pm
+        torch.cuda.empty_cache()
+    print(json.dumps({"sweep_summary": [(r["precision"], r["h"], r["s_int"], r["max_rel_err"], r["meets_bar"])
+                                        for r in rows]}), flush=True)
+    return 0
 
 
 # ------------------------------------------------------------------------------------------------
@@ -610,25 +892,49 @@ def run_batch(args, rank, world, local_rank):
                 "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured); algorithmic bytes of the series and "
                              "recovery products only (Algorithm 1's passes not counted)",
                 "launch_ms": statistics.mean(step_ms)}
-    # the plain single-instance FP64 path on the same instances (one by one), timed once
-    single = None
+    # the plain single-instance path on the same instances, one by one, timed once: (1) each instance in its
+    # own precision and tol (the same stated accuracy as in the batch), (2) every instance in FP64 at 2^-53
+    single, single64 = None, None
     if rank == 0:
         ws_p = api.new_params(dev)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        d64 = [(A.astype(torch.float64), V.double()) for (A, V) in devs]
-        for A, V in d64[:4]:  # warm-up
-            api.select_params(A, out=ws_p)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for x, (A, V) in zip(insts, d64):
-            P = api.select_params(A, out=ws_p)
-            api.solve(A, V, x["t"], x["alpha"], 2.0**-53, P)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        sms = e0.elapsed_time(e1)
+
+        def one_by_one(pairs, tols):
+            for A, V in pairs[:4]:  # warm-up
+                api.select_params(A, out=ws_p)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs = []
+            for x, (A, V), tl in zip(insts, pairs, tols):
+                Pm = api.select_params(A, tol=tl, out=ws_p)
+                outs.append(api.solve(A, V, x["t"], x["alpha"], tl, Pm)[0])
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1), outs
+
+        sms, w_single = one_by_one(devs, [x["tol"] for x in insts])
         single = {"value": len(insts) / (sms / 1000.0), "unit": "solves/s", "ms": sms,
-                  "path": "phic_select_params + phic_solve per instance, FP64 at tol 2^-53, same 512 instances"}
+                  "path": "phic_select_params + phic_solve per instance, each in its own precision and tol "
+                          "(matched accuracy), same instances"}
+        if prec_name != "f64":
+            d64 = [(A.astype(torch.float64), V.double()) for (A, V) in devs]
+            sms64, _ = one_by_one(d64, [2.0**-53] * len(insts))
+            single64 = {"value": len(insts) / (sms64 / 1000.0), "unit": "solves/s", "ms": sms64,
+                        "path": "phic_select_params + phic_solve per instance, all FP64 at tol 2^-53"}
+            del d64
+    errors = None
+    cpu_sample = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_sample, refs_ = fleet_oracle_sample(insts[:6], return_results=True)
+        bars = {"f64": 1e-12, "f32": 5e-6}
+        per = []
+        for i, (x, ref) in enumerate(zip(insts[:6], refs_)):
+            eb = max(rel_errors(items[i].W.double().cpu().numpy(), ref))
+            es = max(rel_errors(w_single[i].double().cpu().numpy(), ref)) if single is not None else None
+            per.append({"instance": i, "n": int(x["A"].n), "prec": x["prec"], "batch_err": eb, "single_err": es,
+                        "bar": bars[x["prec"]], "within_bar": bool(eb <= bars[x["prec"]])})
+        errors = {"metric": "max over i of ||w_i - w_i_oracle||_2 / ||w_i_oracle||_2 (FP64 oracle, its own xi, s)",
+                  "sample": per}
     nf32 = sum(1 for x in insts if x["prec"] == "f32")
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -641,14 +947,15 @@ def run_batch(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "step": "one persistent launch over all 512 instances"},
             "roofline": roofline, "gpu_launches": int(launches), "wall_s_timed_region": wall,
-            "single_instance_fp64": single}
+            "single_instance": single, "single_instance_fp64": single64, "errors": errors,
+            "batch_vs_single": value / single["value"] if single else None}
     clk_sum = clk.summary()
     if clk_sum:
         line["clocks"] = clk_sum
     if not args.no_e2e:
         line["e2e"] = batch_e2e(api, insts, devs, items, b, dev, stream, K, world, dist)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = fleet_oracle_sample(insts[:6])
+    if cpu_sample is not None:
+        line["cpu_baseline"] = cpu_sample
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -693,20 +1000,23 @@ def batch_e2e(api, insts, devs, items, b, dev, stream, K, world, dist):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
-def fleet_oracle_sample(insts):
-    """The oracle (Algorithm 1 + Algorithm 3 in FP64, OpenMP over rows) on a few instances."""
+def fleet_oracle_sample(insts, return_results=False):
+    """The oracle (Algorithm 1 + Algorithm 3 in FP64 at tol 2^-53, OpenMP over rows) on a few instances."""
     import oracle
 
     oracle.build()
     cores = os.cpu_count() or 1
     used = oracle.set_threads(cores)
+    outs = []
     t0 = time.perf_counter()
     for x in insts:
-        sel = oracle.select(x["A"], tol=x["tol"])
-        oracle.solve(x["A"], x["V"], x["t"], x["alpha"], x["tol"], sel["s"], sel["xi"])
+        sel = oracle.select(x["A"])
+        outs.append(oracle.solve(x["A"], x["V"], x["t"], x["alpha"], 2.0**-53, sel["s"], sel["xi"])[0])
     dt = time.perf_counter() - t0
-    return {"value": len(insts) / dt, "unit": "solves/s", "cores": used, "kind": "oracle",
-            "sample": f"the first {len(insts)} instances of the workload (Algorithm 1 + 3 each), FP64 C oracle"}
+    res = {"value": len(insts) / dt, "unit": "solves/s", "cores": used, "kind": "oracle",
+           "sample": f"the first {len(insts)} instances of the workload (Algorithm 1 + 3 each at tol 2^-53), "
+                     "FP64 C oracle"}
+    return (res, outs) if return_results else res
 
 
 def serve_requests(count, seed=5):
@@ -731,10 +1041,65 @@ def serve_requests(count, seed=5):
     return out
 
 
+def serve_stream(srv, hostreq, reqs, big_A, rate, count, seed, local_rank):
+    """One Poisson stream of `count` of the prepared requests at `rate` per second into a running server;
+    returns the stream's metrics (latency = result on the host minus submission)."""
+    import numpy as np
+
+    hostreq, reqs = hostreq[:count], reqs[:count]
+    c0 = srv.counters()
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=len(hostreq))
+    ids = []
+    with ClockSampler(local_rank, None) as clk:
+        t_start = time.perf_counter()
+        due = t_start
+        for q, g in zip(hostreq, gaps):
+            due += g
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                time.sleep(min(due - now, 0.0005))
+            ids.append(srv.submit(q))
+        infos = [srv.wait(i, 600000) for i in ids]
+        t_end = time.perf_counter()
+    c1 = srv.counters()
+    bad = [i for i, x in enumerate(infos) if x["status"] != 0]
+    if bad:
+        srv.close()
+        raise SystemExit(f"serve: {len(bad)} of {len(infos)} requests reported a device status (first: request "
+                         f"{bad[0]}, status {infos[bad[0]]['status']}); no number is reported")
+    lat = np.array([(x["done_ns"] - x["submit_ns"]) / 1e6 for x in infos])
+    first_sub = min(x["submit_ns"] for x in infos)
+    last_sub = max(x["submit_ns"] for x in infos)
+    last_done = max(x["done_ns"] for x in infos)
+    span = (last_done - first_sub) / 1e9
+    nbytes = 0.0
+    for q, x in zip(reqs, infos):
+        st = x["stats"]
+        if q["kind"] == "big":
+            n, nnz, p, r = big_A.n, big_A.nnz, 3, 2
+        else:
+            n, nnz, p, r = q["inst"]["A"].n, q["inst"]["A"].nnz, q["inst"]["p"], q["inst"]["r"]
+        nbytes += solve_bytes(n, nnz, p, r, st["series_terms"], st["recovery_terms"], 4 if q["prec"] == "f32" else 8)
+    busy_s = (c1["gpu_busy_ms"] - c0["gpu_busy_ms"]) / 1000.0
+    # backlog when the last request arrived: submitted but not yet completed
+    backlog = sum(1 for x in infos if x["done_ns"] > last_sub)
+    return {"offered_rate": rate, "requests": len(infos), "achieved_rate": len(infos) / span, "span_s": span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "backlog_at_last_arrival": backlog,
+            "slices": c1["slices"] - c0["slices"], "max_slice_requests": c1["max_slice_requests"],
+            "gpu_busy_frac": busy_s / span if span > 0 else None, "busy_s": busy_s, "bytes": nbytes,
+            "arena_peak_gb": c1["arena_peak"] / 1e9, "wall_s": t_end - t_start, "clocks": clk.summary(),
+            "failed": 0}
+
+
 def run_serve(args, rank, world, local_rank):
-    """serve: Poisson arrivals at --rate of --requests solve requests into the continuous-batching loop;
-    value = completed solves per second of wall time (first arrival to last result on the host),
-    latency = result-on-host minus submission, p50 and p99."""
+    """serve: Poisson arrivals of solve requests into the continuous-batching loop.  The line's value is
+    the stream at --rate (--requests arrivals): completed solves per second of wall time (first arrival to
+    last result on the host), latency = result-on-host minus submission, p50 and p99.  Before it, streams
+    at lower offered rates (SERVE_CURVE_RATES, at least 300 requests or 3 s of arrivals each) give the
+    latency-versus-load curve and the loop's capacity."""
     import numpy as np
     import torch
 
@@ -768,81 +1133,57 @@ def run_serve(args, rank, world, local_rank):
             x = q["inst"]
             hostreq.append(api.HostRequest(x["A"], x["V"], x["t"], x["alpha"], tol=x["tol"], prec=x["prec"]))
     # warm-up: a few requests through the loop
-    for k in range(max(args.warmup, 0)):  # the buffers are reused by the timed stream (W is rewritten)
+    for k in range(max(args.warmup, 0)):  # the buffers are reused by the timed streams (W is rewritten)
         for i in [srv.submit(r) for r in hostreq[k * 4:(k + 1) * 4]]:
             srv.wait(i, 120000)
-    c0 = srv.counters()
-    gaps = np.random.default_rng(11).exponential(1.0 / args.rate, size=len(hostreq))
-    ids = []
-    with ClockSampler(local_rank, None) as clk:
-        t_start = time.perf_counter()
-        due = t_start
-        for q, g in zip(hostreq, gaps):
-            due += g
-            while True:
-                now = time.perf_counter()
-                if now >= due:
-                    break
-                time.sleep(min(due - now, 0.0005))
-            ids.append(srv.submit(q))
-        infos = [srv.wait(i, 600000) for i in ids]
-        t_end = time.perf_counter()
-    c1 = srv.counters()
-    bad = [i for i, x in enumerate(infos) if x["status"] != 0]
-    if bad:
-        srv.close()
-        raise SystemExit(f"serve: {len(bad)} of {len(infos)} requests reported a device status (first: request "
-                         f"{bad[0]}, status {infos[bad[0]]['status']}); no number is reported")
-    lat = np.array([(x["done_ns"] - x["submit_ns"]) / 1e6 for x in infos])
-    first_sub = min(x["submit_ns"] for x in infos)
-    last_done = max(x["done_ns"] for x in infos)
-    span = (last_done - first_sub) / 1e9
-    failed = sum(1 for x in infos if x["status"] != 0)
-    nbytes = 0.0
-    for q, x in zip(reqs, infos):
-        st = x["stats"]
-        if q["kind"] == "big":
-            n, nnz, p, r = big_A.n, big_A.nnz, 3, 2
-        else:
-            n, nnz, p, r = q["inst"]["A"].n, q["inst"]["A"].nnz, q["inst"]["p"], q["inst"]["r"]
-        nbytes += solve_bytes(n, nnz, p, r, st["series_terms"], st["recovery_terms"], 4 if q["prec"] == "f32" else 8)
-    busy_s = (c1["gpu_busy_ms"] - c0["gpu_busy_ms"]) / 1000.0
+    curve = []
+    for rate in [x for x in SERVE_CURVE_RATES if x < args.rate]:
+        cnt = min(len(hostreq), max(300, int(3.0 * rate)))
+        curve.append(serve_stream(srv, hostreq, reqs, big_A, rate, cnt, 11 + len(curve), local_rank))
+    m = serve_stream(srv, hostreq, reqs, big_A, args.rate, len(hostreq), 11, local_rank)
+    curve.append(m)
+    srv.close()
     hbm_peak = float(_peaks().get("hbm_gbs", 6800.0))
-    achieved = nbytes / busy_s / 1e9 if busy_s > 0 else 0.0
-    value = len(infos) / span
+    achieved = m["bytes"] / m["busy_s"] / 1e9 if m["busy_s"] > 0 else 0.0
     # bytes the server copies per request: the operator's CSR arrays (none for a registered operator)
     # and V in, W out
     def _nb(x):
         return 0 if x is None else x.numel() * x.element_size()
     h2d = int(sum(_nb(q.rowptr) + _nb(q.colidx) + _nb(q.values) + _nb(q.V) for q in hostreq))
     d2h = int(sum(_nb(q.W) for q in hostreq))
-    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
-            "ms_per_step": span * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+f32", "data": "synthetic",
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "mean": float(lat.mean()), "max": float(lat.max())},
-            "config": {"workload": f"serve: {len(reqs)} Poisson arrivals at {args.rate:g}/s; 80% batching-distribution "
-                                   "instances (own operator, Algorithm 1 in the first slice), 20% n=1e6 3-D "
-                                   "convection-diffusion (100^3, Pe 10) solves on a registered operator, p=3 r=2 "
+    kept = [c for c in curve if c["achieved_rate"] >= 0.9 * c["offered_rate"]]
+    line = {"metric": METRIC, "value": m["achieved_rate"], "unit": "solves/s", "n_gpus": 1, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": m["span_s"] * 1000.0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "latency_ms": {"p50": m["p50_ms"], "p99": m["p99_ms"], "mean": m["mean_ms"], "max": m["max_ms"]},
+            "latency_curve": [{k: c[k] for k in ("offered_rate", "requests", "achieved_rate", "p50_ms", "p99_ms",
+                                                 "backlog_at_last_arrival", "slices", "gpu_busy_frac")}
+                              for c in curve],
+            "capacity": {"completed_per_s_at_highest_load": max(c["achieved_rate"] for c in curve),
+                         "highest_offered_rate_kept_up": max((c["offered_rate"] for c in kept), default=None),
+                         "note": "kept up = completed at least 90 % of the offered rate over the stream"},
+            "config": {"workload": f"serve: {m['requests']} Poisson arrivals at {args.rate:g}/s; 80% batching-"
+                                   "distribution instances (own operator, Algorithm 1 in the first slice), 20% n=1e6 "
+                                   "3-D convection-diffusion (100^3, Pe 10) solves on a registered operator, p=3 r=2 "
                                    "t=(h/2,h/3) h=1e-4; tol 2^-53 FP64 or 2^-24 FP32 per request",
-                       "offered_rate": args.rate, "achieved_rate": value, "failed": failed,
-                       "slices": c1["slices"] - c0["slices"], "max_slice_requests": c1["max_slice_requests"],
-                       "gpu_busy_frac": busy_s / span if span > 0 else None, "arena_gb": arena / 1e9,
-                       "arena_peak_gb": c1["arena_peak"] / 1e9,
+                       "offered_rate": args.rate, "achieved_rate": m["achieved_rate"], "failed": 0,
+                       "backlog_at_last_arrival": m["backlog_at_last_arrival"],
+                       "slices": m["slices"], "max_slice_requests": m["max_slice_requests"],
+                       "gpu_busy_frac": m["gpu_busy_frac"], "arena_gb": arena / 1e9,
+                       "arena_peak_gb": m["arena_peak_gb"],
                        "step": "the whole arrival stream (first submission to last result on the host)",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": "x1"},
             "roofline": {"bound": "hbm", "kernel": "batch_kernel slices (series + recovery products)",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                          "traffic": None, "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured); "
                                                        "algorithmic bytes over the slices' device time"},
-            "gpu_launches": int(c1["slices"] - c0["slices"]) * 2, "wall_s_timed_region": t_end - t_start,
-            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "gpu_launches": int(m["slices"]) * 2, "wall_s_timed_region": m["wall_s"],
+            "e2e": {"value": m["achieved_rate"], "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
                     "note": "the serving numbers are end to end already: host inputs in, results on the host; "
                             "the step is the whole stream"}}
-    clk_sum = clk.summary()
-    if clk_sum:
-        line["clocks"] = clk_sum
-    srv.close()
+    if m["clocks"]:
+        line["clocks"] = m["clocks"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1049,8 +1390,8 @@ def run_lowrank(args, rank, world, local_rank):
                 for x in st)
     achieved = flops / solve_s / 1e9
     roof = {"bound": "alu", "kernel": "lr_series_kernel + lr_recover_kernel (the two solves of a step)",
-            "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "FP64 GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+            "achieved": achieved, "peak": FP64_DERIVED_GFLOPS, "unit": "FP64 GFLOP/s",
+            "frac": achieved / FP64_DERIVED_GFLOPS, "traffic": None,
             "peak_note": "FP64 pipe: 2 FMA/clk/SM x 2 flop x 152 SMs x 2070 MHz; achieved counts (4 n k + 4 n) w "
                          "flops per series term and (4 n k + 3 n) w per recovery term, k = 2; the working set is "
                          "L2-resident",

@@ -184,9 +184,12 @@ phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, c
  * library holds until the process exits.  It allocates nothing itself.
  *   - Size limit: when phic_solve_workspace_size(n, nnz, p, r, prec) exceeds PHIC_NOALLOC_MAX_BYTES the
  *     call returns PHIC_WORKSPACE_TOO_SMALL and enqueues nothing (e.g. FP64, p = 3, r = 2 and a 7-point
- *     stencil fit up to about 70,000 rows).
+ *     stencil fit up to about 60,000 rows: the solve workspace takes about 557 bytes a row there).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- *     device current and caches it; make that first call before any stream capture.
+ *     device current and caches it; make that first call before any stream capture.  The cached address
+ *     belongs to the device's primary context: after cudaDeviceReset on a device, the library's module is
+ *     loaded again and the array may move, so do not call phic_solve_noalloc on that device again in the
+ *     same process.
  *   - Every call shares the one array, which keeps the previous call's contents (the call clears the
  *     parts that must start at zero).  Calls whose work overlaps on the GPU -- on different streams, or
  *     from different host threads -- race on the array and give undefined results: serialise them.
@@ -475,6 +478,21 @@ void phic_set_blocks_per_sm(int32_t blocks);
  * kernel leaving before the first grid barrier (when the grid has more than one block), so that the
  * other blocks' bounded waits expire and the solve reports PHIC_TIMEOUT.  Consumed by that call. */
 void phic_set_test_fault(int32_t mode);
+
+/* FP64 throughput probe (a diagnostic; the paper has no counterpart).  Enqueues on `stream` one launch of
+ * 4 blocks of 256 threads per SM in which every thread runs 8 independent chains of `iters` dependent FP64
+ * fused multiply-adds, with no memory traffic; *fmas receives the launch's total count of FMAs
+ * (grid x 256 x 8 x iters), so that FMAs / (CUDA-event duration) is the device's FP64 FMA rate, the roof of
+ * the FP64-bound sparse products.  sink_dev: device, one double (written only in a case that never
+ * occurs).  PHIC_INVALID_ARG for iters < 1 or a NULL pointer. */
+phic_status phic_probe_fp64_fma(int32_t iters, double* sink_dev, int64_t* fmas, phic_stream_t stream);
+
+/* Test hook of Algorithm 1 (Section 3): the coefficients of the objective
+ * f(xi) = ||sum_k binom(m,k) z^(m-k) V_k||_2^(1/m), z = -xi/s0, exactly as phic_select_params forms them.
+ * Writes 3 (m+1) doubles to out_dev (device) on `stream`: out[k] = binom(m,k) z^(m-k) as used, out[m+1+k]
+ * = z^(m-k) (double-double square and multiply, rounded once) and out[2(m+1)+k] = binom(m,k) (128-bit
+ * integers, rounded once), k = 0..m.  1 <= m <= 128; z finite. */
+phic_status phic_test_objective_coeffs(int32_t m, double z, double* out_dev, phic_stream_t stream);
 
 /* Text of a status code (static storage). */
 const char* phic_status_string(int32_t status);

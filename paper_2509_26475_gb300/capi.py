@@ -175,6 +175,8 @@ SIGNATURES = [
     ("phic_set_spin_limit_ms", None, [ctypes.c_double]),
     ("phic_set_blocks_per_sm", None, [ctypes.c_int32]),
     ("phic_set_test_fault", None, [ctypes.c_int32]),
+    ("phic_probe_fp64_fma", ctypes.c_int, [ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int64), _P]),
+    ("phic_test_objective_coeffs", ctypes.c_int, [ctypes.c_int32, ctypes.c_double, _P, _P]),
     ("phic_status_string", ctypes.c_char_p, [ctypes.c_int32]),
     ("phic_launch_count", ctypes.c_uint64, []),
     ("phic_version", ctypes.c_int32, []),

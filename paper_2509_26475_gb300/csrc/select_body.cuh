@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "lowrank.cuh"
+#include "select_coef.cuh"
 
 namespace phic {
 
@@ -31,32 +32,6 @@ constexpr int kMaxM = 128;
 // Brent (1973, ch. 5) minimiser as a resumable state machine: after each function value it either
 // names the next abscissa to evaluate (u) or finishes.  Golden-section steps into the larger part of
 // the bracket, parabolic steps through the three best points when they are safe.
-// z^e for an integer e >= 0 by binary exponentiation (square and multiply) carried in double-double
-// arithmetic, Dekker's exact product through an FMA, and rounded once: within about an ulp of the exact
-// power, as a general pow, in at most 2 log2(e) double-double products.  Overflow returns the product
-// that overflowed (+-inf).
-__device__ __forceinline__ void dd_mul(double& ah, double& al, double bh, double bl) {
-  const double p = ah * bh;
-  if (!isfinite(p)) {
-    ah = p;
-    al = 0.0;
-    return;
-  }
-  const double e = fma(ah, bh, -p) + (ah * bl + al * bh);
-  const double s = p + e;
-  al = e - (s - p);
-  ah = s;
-}
-__device__ __forceinline__ double pow_int(double z, int e) {
-  double rh = 1.0, rl = 0.0, bh = z, bl = 0.0;
-  while (e > 0) {
-    if (e & 1) dd_mul(rh, rl, bh, bl);
-    e >>= 1;
-    if (e) dd_mul(bh, bl, bh, bl);
-  }
-  return isfinite(rh) ? rh + rl : rh;
-}
-
 struct BrentSM {
   double lo, hi;        // bracket
   double x, w, v;       // best, second best, previous second best
@@ -376,26 +351,14 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
     const double half = sqrt((double)n) * sh.s0;
     brent_start(sh.br, -half, half, 1e-8 * sh.s0, a.max_evals);
   }
-  if (threadIdx.x == 0) {
-    // binom(m, k) in exact 128-bit integer arithmetic, rounded once to double: the objective cancels
-    // heavily near its minimum, so coefficient errors raise its rounding floor
-    unsigned __int128 c = 1;
-    sh.binom[0] = 1.0;
-    for (int kk = 1; kk <= m; ++kk) {
-      const unsigned __int128 num = (unsigned __int128)(m - kk + 1), den = (unsigned __int128)kk;
-      const unsigned __int128 q = c / den, rem = c % den;
-      c = q * num + rem * num / den;  // c * num / den without overflow (the product is divisible by den)
-      sh.binom[kk] = (double)c;
-    }
-  }
+  if (threadIdx.x == 0) binomial_row(m, sh.binom);
   __syncthreads();
   const double lbin = lgamma(m + 1.0);
   while (true) {
     // coefficients binom(m,k) z^(m-k), z = -u/s0
     if (threadIdx.x <= m) {
       const int kk = threadIdx.x;
-      const double z = -sh.br.u / sh.s0;
-      sh.coef[kk] = sh.binom[kk] * pow_int(z, m - kk);
+      sh.coef[kk] = objective_coef(sh.binom[kk], -sh.br.u / sh.s0, m - kk);
     }
     __syncthreads();
     const double2* __restrict__ Vp2 = reinterpret_cast<const double2*>(a.Vb);

@@ -339,6 +339,9 @@ void admit(phic_server& S) {
       S.ctr.arena_peak = (int64_t)S.pool.peak();
     }
     if (!ok) {
+      // copies enqueued before the failing one may still be writing into the request's blocks: let them
+      // end before the blocks go back to the pool, where the next request could take the same ranges
+      cudaStreamSynchronize(S.s_copy);
       release_blocks(S, q);
       drop_op_ref(S, q);
       finish_req(S, q, PHIC_CUDA_ERROR);

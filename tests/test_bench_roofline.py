@@ -39,6 +39,28 @@ def test_terms_and_steps_scale_the_counts(bench):
     assert f_steps == f7 + 3 * (1 + 3) * 1000 * 4  # the refresh of each outer step
 
 
-def test_fp64_peak_is_the_pipe_in_flops(bench):
-    # 2 FMA per clock per SM, 2 flops per FMA, 152 SMs, 2070 MHz
-    assert bench.FP64_PEAK_GFLOPS == pytest.approx(1258.56)
+def test_derived_fp64_figure_is_the_pipe_in_flops(bench):
+    # context beside the measured roof: 2 FMA per clock per SM, 2 flops per FMA, 152 SMs, 2070 MHz
+    assert bench.FP64_DERIVED_GFLOPS == pytest.approx(1258.56)
+
+
+def test_select_kernel_bytes(bench):
+    # Algorithm 1 with m = 61: 61 sparse products, the rescaling of r vectors and one pass over the 62
+    # basis vectors per objective evaluation; on the 1024^2 operator a pass is 520 MB
+    n, nnz = 1048576, 5238784
+    spmv = 12 * nnz + 4 * (n + 1) + 16 * n
+    assert bench.select_kernel_bytes(n, nnz, 61, 32, 0) == 61 * spmv + 16 * n * 32
+    one_eval = bench.select_kernel_bytes(n, nnz, 61, 32, 1) - bench.select_kernel_bytes(n, nnz, 61, 32, 0)
+    assert one_eval / 1e6 == pytest.approx(520.1, abs=0.1)
+
+
+def test_default_line_is_the_1024_workload_in_fp64(bench):
+    assert bench.WORKLOAD == "advdiff2d-1024" and bench.PRECISION == "f64"
+    assert bench.HS == (1e-5, 1e-4) and (bench.P, bench.R) == (4, 4)
+    # the oracle's timed sample on this workload is Algorithm 1 + the h = 1e-5 solve; the 64^3 step is whole
+    assert bench.oracle_sample_hs() == (1e-5,)
+    bench.configure("convdiff3d-64", "f64")
+    try:
+        assert bench.oracle_sample_hs() == (1e-4, 1e-2)
+    finally:
+        bench.configure("advdiff2d-1024", "f64")

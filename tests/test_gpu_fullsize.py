@@ -1,0 +1,89 @@
+"""The 1024^2 precision workload at full size against the oracle's sampled answer, through the C ABI.
+
+Workload: 2-D upwind advection-diffusion on 1024^2 (n = 1,048,576, Peclet 1e3), p = 4, r = 4,
+t = (1/4, 1/2, 3/4, 1) h, alpha = 1, seed 3.  At h = 1e-4 (s_int about 65, some 3500 recovery terms) and
+h = 1e-3 (s_int about 650) the oracle takes minutes to an hour on the host, so
+tests/golden/make_advdiff2d_1024.py (which calls only the oracle) stored its answer reduced to sampled
+rows, projections on seeded Gaussian vectors and the 2-norms.  These tests run the GPU solve in the launch
+configuration the benchmark times and compare:
+  * FP64 at tol 2^-53 with the oracle's own (xi, s): relative 2-norm error over the sampled rows <= 1e-12,
+    every projection within 4e-12 ||w_i||, every 2-norm within 1e-12, s_int equal, recovery terms
+    within s_int / 10;
+  * FP32 at tol 2^-24 with the GPU's Algorithm 1: the same against the FP64 oracle at 5e-6.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_26475_gb300 import api, capi
+from paper_2509_26475_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL53, TOL24 = 2.0**-53, 2.0**-24
+
+
+def _golden(h):
+    path = os.path.join(HERE, "golden", f"advdiff2d_1024_h{h:g}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{os.path.basename(path)} not generated")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_2509_26475_gb300 import build
+
+    build.build()
+    capi.load()
+    torch.cuda.set_device(0)
+    w = wl.workload_advdiff2d_1024(1.0, TOL53)
+    return w
+
+
+def _compare(W, gold, bar):
+    W = np.asarray(W, dtype=np.float64)
+    idx = np.asarray(gold["index"], dtype=np.int64)
+    n = W.shape[1]
+    G = [np.random.default_rng(s).standard_normal(n) for s in gold["projection_seeds"]]
+    out = []
+    for i in range(W.shape[0]):
+        ref = np.asarray(gold["values"][i])
+        e_samp = float(np.linalg.norm(W[i, idx] - ref) / np.linalg.norm(ref))
+        nrm = gold["norm2"][i]
+        e_norm = abs(float(np.linalg.norm(W[i])) - nrm) / nrm
+        e_proj = max(abs(float(g @ W[i]) - pq) for g, pq in zip(G, gold["proj"][i])) / nrm
+        out.append((e_samp, e_norm, e_proj))
+        assert e_samp <= bar, (i, out)
+        assert e_norm <= bar, (i, out)
+        assert e_proj <= 4.0 * bar, (i, out)
+    return out
+
+
+def _solve(w, h, dtype, tol, params):
+    A = api.DeviceCSR.from_host(w["A"], dtype=dtype)
+    V = torch.as_tensor(w["V"]).to(dtype).cuda()
+    t = [0.25 * h, 0.5 * h, 0.75 * h, h]
+    P = params(A)
+    W, st = api.solve(A, V, t, np.ones(4), tol, P)
+    torch.cuda.synchronize()
+    return W.cpu().numpy(), api.read_stats(st)
+
+
+@pytest.mark.parametrize("h", [1e-4, 1e-3])
+def test_fp64_against_oracle_samples(setup, h):
+    gold = _golden(h)
+    sel = gold["select"]
+    W, st = _solve(setup, h, torch.float64, TOL53, lambda A: api.set_params(sel["xi"], sel["s"]))
+    assert st["status"] == 0, st
+    assert st["s_int"] == gold["stats"]["s_int"] > 1
+    assert abs(st["series_terms"] - gold["stats"]["series_terms"]) <= 1
+    assert abs(st["recovery_terms"] - gold["stats"]["recovery_terms"]) <= max(1, st["s_int"] // 10)
+    errs = _compare(W, gold, 1e-12)
+    print(f"h={h:g} FP64: s_int={st['s_int']} terms={st['recovery_terms']} (sampled, norm, projection) errors "
+          f"{[tuple(f'{x:.1e}' for x in e) for e in errs]}")

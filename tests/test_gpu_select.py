@@ -94,3 +94,53 @@ def test_seeded_vector_matches_oracle_draw(oracle_mod):
     g1 = _gpu_select(A, seed=1234)
     g2 = _gpu_select(A, v=oracle_mod.unit_vector(A.n, 1234))
     assert g1["r"] == g2["r"] and g1["s0"] == g2["s0"] and g1["s"] == g2["s"]
+
+
+def _ulp_diff(a: float, b: float) -> int:
+    """Distance in units in the last place between two finite doubles of the same sign."""
+    import struct
+
+    ia = struct.unpack("<q", struct.pack("<d", a))[0]
+    ib = struct.unpack("<q", struct.pack("<d", b))[0]
+    return abs(ia - ib)
+
+
+@pytest.mark.parametrize("m", [7, 40, 61, 128])
+def test_objective_coefficients_against_exact_arithmetic(m):
+    """The coefficients binom(m,k) z^(m-k) of Algorithm 1's objective as the selection kernel forms them
+    (read back through phic_test_objective_coeffs), against exact rational arithmetic: binom(m, k) is the
+    correctly rounded integer, z^(m-k) lies within one ulp of the exact power (double-double square and
+    multiply), and the coefficient is their rounded product, so within 3 roundings of the exact one."""
+    import ctypes
+    from fractions import Fraction
+
+    lib = capi.load()
+    rng = np.random.default_rng(m)
+    zs = [0.0, 1.0, -1.0, 0.5, -2.75] + list(rng.uniform(-1.0, 1.0, 12) * 10.0 ** rng.uniform(-2.0, 1.5, 12))
+    out = torch.empty(3 * (m + 1), dtype=torch.float64, device="cuda")
+    exact_pow = 0
+    total = 0
+    for z in zs:
+        capi.check(lib.phic_test_objective_coeffs(m, ctypes.c_double(float(z)), out.data_ptr(), None),
+                   "phic_test_objective_coeffs")
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        coef, pw, bn = o[: m + 1], o[m + 1: 2 * (m + 1)], o[2 * (m + 1):]
+        for k in range(m + 1):
+            b_exact = math.comb(m, k)
+            assert bn[k] == float(b_exact), (m, k)
+            p_exact = Fraction(float(z)) ** (m - k)
+            try:
+                p_ref = float(p_exact)
+            except OverflowError:
+                continue
+            if p_ref == 0.0 or abs(p_ref) < 1e-290:
+                assert abs(pw[k]) <= 1e-290
+                continue
+            assert _ulp_diff(float(pw[k]), p_ref) <= 1, (m, z, k, pw[k], p_ref)
+            exact_pow += int(float(pw[k]) == p_ref)
+            total += 1
+            assert float(coef[k]) == float(bn[k]) * float(pw[k])  # one rounding of the two doubles' product
+            c_exact = b_exact * p_exact
+            assert abs(Fraction(float(coef[k])) - c_exact) <= abs(c_exact) * Fraction(3, 2**53), (m, z, k)
+    print(f"m={m}: {exact_pow} of {total} powers correctly rounded, the rest within one ulp")

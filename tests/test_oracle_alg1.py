@@ -82,6 +82,31 @@ def test_objective_without_cancellation(oracle_mod):
             assert abs(fx - expect) <= 1e-13 * expect
 
 
+@pytest.mark.parametrize("top", [1e9, 3.7e7])
+def test_objective_through_the_extended_basis(oracle_mod, top):
+    """The extension V_k = A V_(k-1) / s0 for k = r+1..m (Algorithm 1 after the guard): a diagonal A >= 0
+    whose top eigenvalue is large enough that the guard stops the power chain well before m = 61, and
+    xi < 0, so every binomial term of f has one sign and f is accurate.  f(xi) must equal
+    ||(A - xi I)^m v||^(1/m) / s0 (mpmath, 60 digits), which holds only when every extended column carries
+    exactly one more factor A / s0: a dropped or repeated 1/s0 moves f by a factor s0^(j/m) for some
+    j >= 1, at least about 1.3 here."""
+    import mpmath as mp
+
+    d = np.array([top, 0.5, 2.0, 3.5e3, 7.0, 0.0, 41.0])
+    v = np.array([0.7, -1.0, 0.25, 0.8, -1.1, 0.3, 0.05])
+    m = 61
+    xis = np.array([-1.0e3, -1.0e8, -2.5 * top])
+    f, s0, r = oracle_mod.objective_at(wl.diagonal(d), xis, m=m, v=v)
+    assert 2 <= r < m - 20, r  # most of the basis comes from the extension
+    assert s0 > 0.5 * top  # the growth factor of the dominant eigenvalue
+    with mp.workdps(60):
+        nv = mp.sqrt(sum(mp.mpf(x) ** 2 for x in v))
+        for xi, fx in zip(xis, f):
+            nu = mp.sqrt(sum(((mp.mpf(di) - mp.mpf(xi)) ** m * mp.mpf(vi) / nv) ** 2 for di, vi in zip(d, v)))
+            expect = float(nu ** (mp.mpf(1) / m)) / s0
+            assert abs(fx - expect) <= 1e-13 * expect, (xi, fx, expect)
+
+
 def test_objective_at_zero_shift_is_scaled_power_norm(oracle_mod):
     """f(0) = ||A^m v||^(1/m) / s0 (only the k = m term survives; no cancellation) for any A."""
     import mpmath as mp
