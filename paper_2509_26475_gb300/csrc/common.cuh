@@ -97,6 +97,50 @@ __device__ __forceinline__ bool team_sync_lead(Team& tm, Pre&& pre, Post&& post)
   return s_ok2 != 0;
 }
 
+// As team_sync_lead, but post() runs in every lane of warp 0 (lane 0 still signals the arrival and waits).
+// On GB300 an FP64 instruction occupies the FP64 pipe for a whole warp however few of its lanes are
+// active, so scalar FP64 work for several combinations is spread over the lanes, one combination each,
+// and costs what one combination costs.  The lanes see the other members' writes after lane 0's acquire
+// through the warp barrier, as the block's threads do after the block barrier.
+// prep() runs first, in every lane of warp 0: loads issued there (say, of the next term's constants) travel
+// while lane 0 waits, and post() finds them in registers.
+template <typename Prep, typename Pre, typename Post>
+__device__ __forceinline__ bool team_sync_lead_w(Team& tm, Prep&& prep, Pre&& pre, Post&& post) {
+  __shared__ int s_ok3;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int ok = 1;
+    prep();
+    if (threadIdx.x == 0) {
+      pre();
+      tm.epoch += 1;
+      if (tm.size > 1) {
+        const unsigned long long target = tm.epoch * (unsigned long long)tm.size;
+        bar_arrive(&tm.ctl->bar);
+        if (bar_load(&tm.ctl->bar) < target) {
+          const unsigned long long t0 = global_ns();
+          unsigned spins = 0;
+          while (bar_load(&tm.ctl->bar) < target) {
+            if ((++spins & 31u) == 0 && global_ns() - t0 > tm.spin_ns) {
+              ok = 0;
+              set_status(tm.ctl, PHIC_TIMEOUT);
+              break;
+            }
+          }
+        }
+      } else {
+        __threadfence();
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) post();
+    __syncwarp();
+    if (threadIdx.x == 0) s_ok3 = ok;
+  }
+  __syncthreads();
+  return s_ok3 != 0;
+}
+
 __device__ __forceinline__ bool team_sync(Team& tm) {
   return team_sync_lead(tm, [] {}, [] {});
 }

@@ -37,6 +37,24 @@ struct SolveState {
   int ell;        // copy of B: ELL with this many slots per row, or 0 for CSR order
   int ndia;       // copy of B: DIA with these diagonals (ndia > 0; takes precedence over ell)
   int dia_off[16];
+  // product of the undo factors applied so far, per combination: (pm_h + pm_l) 2^pe (see recover_body)
+  double pm_h[PHIC_MAX_R];
+  double pm_l[PHIC_MAX_R];
+  int pe[PHIC_MAX_R];
+  int coef_k;  // terms k = 1..coef_k of the recovery's coefficient table are filled
+};
+
+// The recovery's Taylor coefficients c_k = (t_i 2^eA / s)^k / k!, the same in every recovery step, filled
+// for k <= kCoefTab the first time a step reaches k: the double-double value and its two neighbours in the
+// tile type with the probability of rounding up (thr / 2^32), so that later steps round it without bias
+// using integer operations only (see recover_body).
+constexpr int kCoefTab = 128;
+template <typename T>
+struct CoefEntry {
+  double ch, cl;  // c_k = ch + cl
+  T base, alt;    // c_k's nearest value in T and its neighbour on the side of the remainder
+  unsigned thr;   // alt is taken when a 32-bit uniform number is below thr
+  float fcoef;    // c_k in FP32, for the norm of the term
 };
 
 // Entry of the solve's copy of A_1 = A - xi I, scaled by 2^-eA: column and value in one aligned load.
@@ -77,6 +95,7 @@ struct SolveArgs {
   Ctl* ctlS;
   Ctl* ctlR;
   SolveState* state;
+  void* coeftab;          // CoefEntry<T>[kCoefTab][PHIC_MAX_R]
   phic_stats* stats;
   unsigned long long spin_ns;
   int fault;

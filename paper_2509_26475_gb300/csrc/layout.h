@@ -42,7 +42,7 @@ inline SelectLayout select_layout(int64_t n, int m) {
 inline long long a1_capacity(long long nnz) { return (nnz > 0 ? nnz : 1) + nnz / 4 + 64; }
 
 struct SolveLayout {
-  size_t ctlS, ctlR, state, A1, rowflag, Vt[2], Dt[2], S, Ft[2], E, total;
+  size_t ctlS, ctlR, state, A1, rowflag, coef, Vt[2], Dt[2], S, Ft[2], E, total;
   long long a1_cap;
   TileLayout sl, fl;
 };
@@ -61,6 +61,7 @@ inline SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec) 
   L.a1_cap = a1_capacity(nnz);
   L.A1 = off; off += align_up((size_t)L.a1_cap * 2 * es);  // (column, value) entries, CSR or ELL order
   L.rowflag = off; off += align_up((size_t)n);
+  L.coef = off; off += align_up((size_t)kCoefTab * PHIC_MAX_R * sizeof(CoefEntry<double>));
   for (int q = 0; q < 2; ++q) { L.Vt[q] = off; off += tileS; }
   for (int q = 0; q < 2; ++q) { L.Dt[q] = off; off += tileS; }
   L.S = off; off += tileS;
@@ -121,6 +122,7 @@ inline void fill_solve_args(SolveArgs& a, const phic_csr* A, int p, int r, const
   a.ctlS = reinterpret_cast<Ctl*>(base + L.ctlS);
   a.ctlR = reinterpret_cast<Ctl*>(base + L.ctlR);
   a.state = reinterpret_cast<SolveState*>(base + L.state);
+  a.coeftab = base + L.coef;
   a.stats = stats_dev;
   a.spin_ns = spin_ns;
   a.fault = 0;

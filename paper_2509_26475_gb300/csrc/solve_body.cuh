@@ -123,6 +123,10 @@ __device__ __forceinline__ double slot_norm(const Ctl* c, int phase, int idx, in
   const unsigned long long u = *(volatile const unsigned long long*)&c->slot[phase & 3][idx];
   return ldexp((double)__int_as_float((int)(unsigned)u), e0);
 }
+// The same norm as the FP32 value it was summed as (scaled by 2^-e0).
+__device__ __forceinline__ float slot_normf(const Ctl* c, int phase, int idx) {
+  return __int_as_float((int)(unsigned)*(volatile const unsigned long long*)&c->slot[phase & 3][idx]);
+}
 __device__ __forceinline__ bool slot_nonfinite(const Ctl* c, int phase) {
   return *(volatile const unsigned long long*)&c->slot[phase & 3][2] != 0ull;
 }
@@ -417,9 +421,61 @@ struct SeriesScalars {
   int dia_off[16];
 };
 
+// ---- scalars of the recovery steps in double-double (warp 0) --------------------------------------
+// Every recovery step applies the same scalars: the Taylor coefficients c_k = (t_i 2^eA / s)^k / k! and
+// the undo factor mu_i = e^(xi t_i / s).  Rounded once and reused, each would carry the same relative
+// error into all s - 1 steps, and those errors would add up coherently: mu's rounding alone (its argument
+// rounded, then magnified |xi t / s| times by the exponential) costs up to about |xi t| 2^-53 in the result,
+// 1.6e-11 at xi t = -1.4e6 (the paper's Chebyshev example at t = 1).  Instead:
+//   - c_k is formed in double-double and rounded to the tile type without bias: up with the probability
+//     of the remainder's share of the gap, decided by a hash of the step, term and combination (next_coefs),
+//     so that the rounding errors of different steps are independent with mean zero;
+//   - the factor applied in step j is chosen so that the product of all applied factors stays within one
+//     rounding of e^(j xi t / s), computed from a double-double exponent (compensated scaling).
+struct DD {
+  double h, l;
+};
+__device__ __forceinline__ DD dd_renorm(double s, double e) {
+  const double h = s + e;
+  return DD{h, e - (h - s)};
+}
+__device__ __forceinline__ DD dd_prod(double a, double b) {
+  const double p = a * b;
+  return DD{p, fma(a, b, -p)};
+}
+__device__ __forceinline__ DD dd_times(DD a, DD b) {
+  const double p = a.h * b.h;
+  return dd_renorm(p, fma(a.h, b.h, -p) + (a.h * b.l + a.l * b.h));
+}
+__device__ __forceinline__ DD dd_times_d(DD a, double b) {
+  const double p = a.h * b;
+  return dd_renorm(p, fma(a.h, b, -p) + a.l * b);
+}
+__device__ __forceinline__ DD dd_over_d(DD a, double d) {
+  const double q = a.h / d;
+  const double rem = fma(-q, d, a.h);  // exact remainder of the leading quotient
+  return dd_renorm(q, (rem + a.l) / d);
+}
+
+// 64 uniform bits from a 64-bit key (the splitmix64 output function).
+__device__ __forceinline__ unsigned long long unit_bits(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+constexpr double kLog2eHi = 1.4426950408889634, kLog2eLo = 2.0355273740931033e-17;  // 1/ln 2 in double-double
+
+// Shared memory of the recovery is tight (one block's rows of E sit next to it at 3 blocks per SM), so the
+// double-double scalars keep their leading parts in the plain arrays: tB + tBl = t_i 2^eA / s and
+// c + cl = c_k; the applied product of the undo factors is (pmh + pml) 2^pe.
 template <typename T>
 struct RecoverScalars {
-  double xi, tB[PHIC_MAX_R], mu[PHIC_MAX_R], c[PHIC_MAX_R];
+  double xi, tB[PHIC_MAX_R], tBl[PHIC_MAX_R], c[PHIC_MAX_R], cl[PHIC_MAX_R];
+  double pmh[PHIC_MAX_R], pml[PHIC_MAX_R];
+  int pe[PHIC_MAX_R];
+  T mu_step[PHIC_MAX_R];  // the undo factor of the current step
   T coef[PHIC_MAX_R];
   float fcoef[PHIC_MAX_R];
   T cj[PHIC_MAX_P + 1][PHIC_MAX_R];
@@ -438,11 +494,25 @@ struct SeriesSmem {
   SeriesTerm<T> tk;
   WarpParts wp;
 };
+// The recovery's loop decisions, kept by warp 0 between two barriers (in shared memory, so that none of it
+// holds a register of the Taylor loop).  The truncation test compares FP32 norms scaled by 2^-e0 as the row
+// sums are formed (R16): c1, c2 and nE are those scaled values.  The leader's block also keeps the counts.
+struct DecideState {
+  double cF;          // ||F||_inf at the start of the current step
+  float c1, c2, nE;
+  int status, k, e0;
+  int cur_j;          // recovery step of the current Taylor loop
+  int tab_k;          // coefficient table filled up to this term (see next_coefs)
+  int max_inner;
+  long long rec_terms;
+};
+
 template <typename T>
 struct RecoverSmem {
   RecoverScalars<T> sc;
   LoopCtl lc;
   WarpParts wp;
+  DecideState ds;
 };
 template <typename T>
 struct LowRankSmem {
@@ -474,7 +544,14 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
   if (threadIdx.x == 0) {
     // s <- ceil(s max|t_i|);  mu = exp((xi/s) T);  V <- V (I kron 1^T mu/s);
     // Jsh = (J kron Delta - xi I kron T)/s  (divided by s as in Algorithm 2)
-    const double xi = a.params->xi;
+    // FP32 storage uses xi rounded to FP32.  The shift is undone exactly by mu whatever its value, but
+    // the diagonal a_ii - xi of B is rounded to FP32 once and then applied in every product: with xi not
+    // an FP32 number, a constant diagonal makes that rounding one shift error delta on every row, which no
+    // step undoes and which costs a relative delta t_i in w_i (about 1e-5 at t = 1e-4 on the 1024^2
+    // advection-diffusion operator, where ulp(a_ii - xi) = 0.25).  With xi in FP32, a_ii - xi is exact
+    // whenever a_ii lies within a factor 2 of xi (Sterbenz), as it does for stencil operators, whose
+    // spectral centre is near their diagonal.
+    const double xi = sizeof(T) == 4 ? (double)__double2float_rn(a.params->xi) : a.params->xi;
     double s = a.params->s;
     if (sizeof(T) == 4) {
       // FP32 storage: the Taylor terms of a step grow like e^(nu t / s) before they cancel, and their
@@ -931,6 +1008,116 @@ __device__ __forceinline__ void jt_power_coeffs(RecoverScalars<T>& rs, const Sol
   }
 }
 
+// The undo factor of recovery step j for each combination (thread 0): the product of the factors applied
+// in steps 1..j is to equal e^(j x_i), x_i = xi t_i / s.  With the applied product P = pm 2^pe (pm in
+// double-double) and j x_i / ln 2 = N + f (N an integer, |f| <= 1/2, from the double-double x_i), the
+// factor is 2^(N - pe) 2^f / pm rounded to the tile type; P then takes it exactly.  The product stays
+// within about one rounding of e^(j x_i) whatever j is.  Where that target leaves the double range (the
+// factor or the product underflows), the plain e^(x_i) of the paper is applied.  Run by the lanes of
+// warp 0, lane i for combination i.
+// The table entry of a coefficient c (double-double): its nearest value in T, the neighbour on the side of
+// the remainder and the probability of rounding to that neighbour, as a 32-bit threshold.
+template <typename T>
+__device__ __forceinline__ CoefEntry<T> coef_entry(DD c);
+template <>
+__device__ __forceinline__ CoefEntry<double> coef_entry<double>(DD c) {
+  CoefEntry<double> e{c.h, c.l, c.h, c.h, 0u, (float)c.h};
+  if (c.l != 0.0 && isfinite(c.h)) {
+    e.alt = nextafter(c.h, c.l > 0.0 ? INFINITY : -INFINITY);
+    e.thr = (unsigned)fmin(c.l / (e.alt - c.h) * 4294967296.0, 4294967295.0);
+  }
+  return e;
+}
+template <>
+__device__ __forceinline__ CoefEntry<float> coef_entry<float>(DD c) {
+  const float f = __double2float_rn(c.h);
+  CoefEntry<float> e{c.h, c.l, f, f, 0u, f};
+  if (isfinite(f)) {
+    const double rem = (c.h - (double)f) + c.l;  // c - f (the first difference is exact)
+    if (rem != 0.0) {
+      e.alt = nextafterf(f, rem > 0.0 ? INFINITY : -INFINITY);
+      e.thr = (unsigned)fmin(rem / ((double)e.alt - (double)f) * 4294967296.0, 4294967295.0);
+    }
+  }
+  return e;
+}
+
+// c_k of recovery step j for every combination, rounded to the tile type without bias: up with the
+// probability of the remainder's share of the gap, decided by a hash of (j, k, i), so that the rounding
+// errors of different steps are independent with mean zero.  Run by the lanes of warp 0, lane i for
+// combination i.  The double-double recursion c_k = c_(k-1) (t_i 2^eA / s) / k runs only the first time a
+// step reaches k (tab_k: terms already in the table); later steps read the table and round with integer
+// operations (on GB300 each FP64 instruction of one lane costs the FP64 pipe a whole warp's time, and this
+// sits between every two Taylor terms).  Out of line, so that the Taylor loop keeps its registers.
+// c_k of combination i from c_(k-1) (in sc.c, sc.cl) by the double-double recursion, entered in the table
+// when k <= kCoefTab: the first time a step reaches k (out of line: it runs rarely, and the Taylor loop keeps
+// its registers).
+template <typename T>
+__device__ __noinline__ CoefEntry<T> coef_new(RecoverScalars<T>& sc, CoefEntry<T>* __restrict__ tab, int i, int k) {
+  const DD tBd{sc.tB[i], sc.tBl[i]};
+  const DD cd = k == 1 ? tBd : dd_over_d(dd_times(DD{sc.c[i], sc.cl[i]}, tBd), (double)k);
+  const CoefEntry<T> e = coef_entry<T>(cd);
+  if (k <= kCoefTab) tab[(size_t)(k - 1) * PHIC_MAX_R + i] = e;
+  return e;
+}
+
+// pf: the entry of (k, lane) when the caller loaded it already (pf_ok), see prefetch_coef.
+template <typename T>
+__device__ __forceinline__ void next_coefs(RecoverScalars<T>& sc, CoefEntry<T>* __restrict__ tab, int tab_k, int r,
+                                           int k, int j, const CoefEntry<T>& pf, bool pf_ok) {
+  const int i = threadIdx.x & 31;
+  if (i >= r) return;  // r <= PHIC_MAX_R < 32: one combination per lane
+  CoefEntry<T> e;
+  if (pf_ok) {
+    e = pf;
+  } else if (k <= tab_k) {
+    e = tab[(size_t)(k - 1) * PHIC_MAX_R + i];
+  } else {
+    e = coef_new(sc, tab, i, k);
+  }
+  sc.c[i] = e.ch;
+  sc.cl[i] = e.cl;
+  const unsigned long long key = ((unsigned long long)j << 32) ^ ((unsigned long long)k << 8) ^ (unsigned long long)i;
+  sc.coef[i] = (unsigned)(unit_bits(key) >> 32) < e.thr ? e.alt : e.base;
+  sc.fcoef[i] = e.fcoef;
+}
+
+// The table entry of term k for this lane's combination, if the table has it (loaded while the team
+// barrier waits; next_coefs takes it from the register).
+template <typename T>
+__device__ __forceinline__ bool prefetch_coef(const CoefEntry<T>* __restrict__ tab, int tab_k, int r, int k,
+                                              CoefEntry<T>& pf) {
+  const int i = threadIdx.x & 31;
+  if (k > tab_k || i >= r) return false;
+  pf = tab[(size_t)(k - 1) * PHIC_MAX_R + i];
+  return true;
+}
+
+template <typename T>
+__device__ __noinline__ void undo_factors(RecoverScalars<T>& sc, const double* t, int r, int j) {
+  for (int i = threadIdx.x & 31; i < r; i += 32) {
+    const DD x = dd_over_d(dd_prod(sc.xi, t[i]), (double)sc.s_int);  // x_i = xi t_i / s
+    const DD y = dd_times(dd_times_d(x, (double)j), DD{kLog2eHi, kLog2eLo});
+    const double N = rint(y.h);
+    const T plain = (T)exp(x.h);  // the paper's e^(x_i), for targets outside the double range
+    sc.mu_step[i] = plain;
+    if (!(fabs(N) < 1e6)) continue;
+    const double f = (y.h - N) + y.l;
+    const double ph = sc.pmh[i], pl = sc.pml[i];
+    double q = exp2(f) / ph;
+    q -= q * (pl / ph);
+    const double mu = ldexp(q, (int)N - sc.pe[i]);
+    const T muT = (T)mu;
+    const DD np = dd_times_d(DD{ph, pl}, (double)muT);
+    if (!(muT != T(0)) || !isfinite(mu) || !(np.h != 0.0) || !isfinite(np.h)) continue;
+    int ex = 0;
+    sc.pmh[i] = frexp(np.h, &ex);
+    sc.pml[i] = ldexp(np.l, -ex);
+    sc.pe[i] += ex;
+    sc.mu_step[i] = muT;
+  }
+}
+
 // Recovery step j: F_k = A_1 F_{k-1} T / (s k) is carried as F_k = c_k G_k with G_k = B G_{k-1},
 // G_0 = F and c_k = c_{k-1} t_i 2^eA / (s k) per column, so that E <- E + F_k is fma(c_k, G_k, E).
 //
@@ -973,22 +1160,41 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
     if (sc.status == PHIC_OK) {
       const double sB = ldexp(1.0, sc.eA);
       for (int i = 0; i < r; ++i) {
-        sc.tB[i] = a.t[i] * sB / sc.s_int;            // T <- I_2 kron T/s, times 2^eA for B
-        sc.mu[i] = exp(sc.xi * a.t[i] / sc.s_int);     // mu <- I_2 kron mu
+        const DD tBd = dd_over_d(DD{a.t[i] * sB, 0.0}, (double)sc.s_int);  // T <- I_2 kron T/s, times 2^eA for B
+        sc.tB[i] = tBd.h;
+        sc.tBl[i] = tBd.l;
+        if (sc.rec_init) {  // a later slice: the product of the undo factors applied so far
+          sc.pmh[i] = vs->pm_h[i];
+          sc.pml[i] = vs->pm_l[i];
+          sc.pe[i] = vs->pe[i];
+        } else {
+          sc.pmh[i] = 1.0;
+          sc.pml[i] = 0.0;
+          sc.pe[i] = 0;
+        }
       }
     }
   }
   __syncthreads();
   if (sc.done) return 1;  // finished in an earlier launch
   const bool leader = tm.rank == 0 && threadIdx.x == 0;
-  long long rec_terms = 0;  // the leader keeps the counts
-  int max_inner = 0;
-  if (leader) {
-    rec_terms = vs->rec_terms;
-    max_inner = vs->max_inner;
+  DecideState& ds = sm.ds;
+  if (threadIdx.x == 0) {
+    ds.status = PHIC_OK;
+    ds.k = 0;
+    ds.e0 = 0;
+    ds.cur_j = 0;
+    ds.tab_k = sc.rec_init ? vs->coef_k : 0;
+    ds.cF = sc.cF0;
+    ds.c1 = ds.c2 = ds.nE = 0.f;
+    ds.rec_terms = vs->rec_terms;
+    ds.max_inner = vs->max_inner;
   }
+  __syncthreads();
   auto finish = [&](int st) {
     if (leader) {
+      const long long rec_terms = ds.rec_terms;
+      const int max_inner = ds.max_inner;
       if (st != PHIC_OK) set_status(ctl, st);
       const int s1 = read_status(a.ctlS);
       int fin = s1 != PHIC_OK ? s1 : read_status(ctl);
@@ -1038,9 +1244,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   auto col_i = [&](int j) { const int c = c0 + j; return c >= L.w ? 0 : (c < r ? c : c - r); };
   int bad = 0;
 
-  // thread-0 loop state
-  int status = PHIC_OK, k = 0, e0 = 0;
-  double cF = sc.cF0, c1 = 0.0, c2 = 0.0, nE = 0.0;
+  CoefEntry<T>* __restrict__ ctab = static_cast<CoefEntry<T>*>(a.coeftab);
   int cur = sc.cur;
 
   // ---- F = S(:, [blk 0, blk p]);  F(:,1:r) <- A F(:,1:r) T + v0 1^T (unshifted A, t undivided) -----
@@ -1095,12 +1299,17 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
     }
     warp_parts(wp, mx, 0ull, bad);
     cur = 0;
-    if (!team_sync_lead(tm, [&] { parts_to_slots(ctl, ph, wp); },
-                        [&] {
-                          status = read_status(ctl);
-                          cF = slot_get(ctl, ph, 0);
-                          lc.status = status;
-                        })) {
+    if (!team_sync_lead_w(tm, [] {}, [&] { parts_to_slots(ctl, ph, wp); },
+                          [&] {
+                            const int st = read_status(ctl);
+                            const double f = slot_get(ctl, ph, 0);
+                            __syncwarp();
+                            if (threadIdx.x == 0) {
+                              ds.status = st;
+                              ds.cF = f;
+                              lc.status = st;
+                            }
+                          })) {
       finish(PHIC_TIMEOUT);
       return 1;
     }
@@ -1113,7 +1322,9 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   // argument fields used per row, kept in registers (the argument block may live in shared memory)
   const int* __restrict__ rowptr = a.rowptr;
   const unsigned char* __restrict__ rowflag = a.rowflag;
-  const double tol = a.tol;
+  // tol in FP32 for the test on the scaled norms (a tol below the FP32 range stops no loop before max_terms,
+  // as a tol of 0 would not)
+  const float tolf = (float)(a.tol > 0x1.0p-125 ? a.tol : 0x1.0p-125);
   const int max_terms = a.max_terms;
   const int ell = sc.ell;
   const int ndia = sc.ndia;
@@ -1121,26 +1332,28 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   dor.load(sc.dia_off, ndia);
   const SpmmOps<T> ops{rowptr, ent, n, ell, ndia, sc.dia_off};
 
-  // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||: next term
-  auto decide = [&]() {
+  // E = F; k = 0; c1 = inf; c2 = ||F||;  while c1 + c2 > tol ||E||: next term.  Run by every lane of warp 0
+  // on its own copy d of the state (identical in all lanes); lane 0 stores it back.
+  auto decide = [&](DecideState& d, const CoefEntry<T>& pf, bool pf_ok) {
     int go = 0;
-    if (status == PHIC_OK && (!isfinite(c2) || !isfinite(nE))) status = PHIC_NONFINITE;
-    if (status == PHIC_OK && c1 + c2 > tol * nE) {
-      if (k >= max_terms) status = PHIC_TERM_CAP;
+    if (d.status == PHIC_OK && (!isfinite(d.c2) || !isfinite(d.nE))) d.status = PHIC_NONFINITE;
+    if (d.status == PHIC_OK && d.c1 + d.c2 > tolf * d.nE) {
+      if (d.k >= max_terms) d.status = PHIC_TERM_CAP;
       else {
-        k += 1;
-        c1 = c2;
+        d.k += 1;
+        d.c1 = d.c2;
         go = 1;
-        for (int i = 0; i < r; ++i) {
-          sc.c[i] = k == 1 ? sc.tB[i] : sc.c[i] * sc.tB[i] / k;  // c_k = (t_i 2^eA / s)^k / k!
-          sc.coef[i] = (T)sc.c[i];
-          sc.fcoef[i] = (float)sc.c[i];
-        }
+        next_coefs(sc, ctab, d.tab_k, r, d.k, d.cur_j, pf, pf_ok);
+        if (d.k > d.tab_k && d.k <= kCoefTab) d.tab_k = d.k;
       }
     }
-    lc.go = go;
-    lc.k = k;
-    lc.status = status;
+    __syncwarp();
+    if (threadIdx.x == 0) {
+      ds = d;
+      lc.go = go;
+      lc.k = d.k;
+      lc.status = d.status;
+    }
   };
 
   // ---- for j = 1 : s-1 ------------------------------------------------------------------------------
@@ -1152,14 +1365,16 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
   bool timed_out = false;
   loop_format<kSplit, LR>(ndia, ell, [&](auto lfmt) {
   for (; jstep <= sc.s_int - 1 && jstep <= j_stop && lc.status == PHIC_OK; ++jstep) {
-    if (threadIdx.x == 0) {
-      k = 0;
-      c1 = INFINITY;
-      c2 = cF;
-      nE = cF;
-      e0 = scale_exponent(cF);  // norms of this step's terms are carried in FP32 scaled by 2^-e0
-      set_norm_scale(lc, e0);
-      decide();
+    if (threadIdx.x < 32) {
+      DecideState d = ds;
+      d.k = 0;
+      d.cur_j = jstep;
+      d.e0 = scale_exponent(d.cF);  // norms of this step's terms are carried in FP32 scaled by 2^-e0
+      d.c1 = INFINITY;
+      d.c2 = (float)ldexp(d.cF, -d.e0);
+      d.nE = d.c2;
+      if (threadIdx.x == 0) set_norm_scale(lc, d.e0);
+      decide(d, CoefEntry<T>{}, false);
     }
     __syncthreads();
     while (lc.go) {
@@ -1239,21 +1454,25 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
       });
       warp_parts(wp, mF, mE, 0, nf);
       cur ^= 1;
-      if (!team_sync_lead(tm, [&] { parts_to_slots(ctl, ph, wp); },
-                          [&] {
-                            status = read_status(ctl);
-                            if (status == PHIC_OK && slot_nonfinite(ctl, ph)) status = PHIC_NONFINITE;
-                            c2 = slot_norm(ctl, ph, 0, e0);
-                            nE = slot_norm(ctl, ph, 1, e0);
-                            decide();
-                          })) {
+      CoefEntry<T> pf;  // the next term's coefficient entry of this lane, loaded while the barrier waits
+      bool pf_ok = false;
+      if (!team_sync_lead_w(tm, [&] { pf_ok = prefetch_coef(ctab, ds.tab_k, r, ds.k + 1, pf); },
+                            [&] { parts_to_slots(ctl, ph, wp); },
+                            [&] {
+                              DecideState d = ds;
+                              d.status = read_status(ctl);
+                              if (d.status == PHIC_OK && slot_nonfinite(ctl, ph)) d.status = PHIC_NONFINITE;
+                              d.c2 = slot_normf(ctl, ph, 0);
+                              d.nE = slot_normf(ctl, ph, 1);
+                              decide(d, pf, pf_ok);
+                            })) {
         timed_out = true;
         return;
       }
     }
     if (leader) {
-      rec_terms += lc.k;
-      max_inner = lc.k > max_inner ? lc.k : max_inner;
+      ds.rec_terms += lc.k;
+      ds.max_inner = lc.k > ds.max_inner ? lc.k : ds.max_inner;
     }
     if (lc.status != PHIC_OK) break;
 
@@ -1261,6 +1480,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
     const int ph = phase++;
     slot_reset(tm, ph);
     jt_power_coeffs(sc, a, jstep);
+    if (threadIdx.x < 32) undo_factors(sc, a.t, r, jstep);
     __syncthreads();
     {
       T* __restrict__ F = static_cast<T*>(a.Ft[cur]);
@@ -1275,7 +1495,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
           VecIO<T, CW>::ld(E + o, e);
 #pragma unroll
           for (int j = 0; j < CW; ++j) {
-            T v = col_live(j) ? e[j] * (T)sc.mu[col_i(j)] : T(0);
+            T v = col_live(j) ? e[j] * sc.mu_step[col_i(j)] : T(0);
             if (col_blkp(j)) {
               const int i = col_i(j);
               const T* srow = S + (size_t)row * ws_s;
@@ -1290,12 +1510,17 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
         if (act && lane == 0) umax(mx, (double)rs);
       }
       warp_parts(wp, mx, 0ull, 0);
-      if (!team_sync_lead(tm, [&] { parts_to_slots(ctl, ph, wp); },
-                          [&] {
-                            cF = slot_get(ctl, ph, 0);
-                            status = read_status(ctl);
-                            lc.status = status;
-                          })) {
+      if (!team_sync_lead_w(tm, [] {}, [&] { parts_to_slots(ctl, ph, wp); },
+                            [&] {
+                              const double f = slot_get(ctl, ph, 0);
+                              const int st = read_status(ctl);
+                              __syncwarp();
+                              if (threadIdx.x == 0) {
+                                ds.cF = f;
+                                ds.status = st;
+                                lc.status = st;
+                              }
+                            })) {
         timed_out = true;
         return;
       }
@@ -1313,10 +1538,16 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
       SolveState* sw = a.state;
       sw->rec_init = 1;
       sw->j_done = jstep - 1;
+      sw->coef_k = ds.tab_k;
+      for (int i = 0; i < r; ++i) {
+        sw->pm_h[i] = sc.pmh[i];
+        sw->pm_l[i] = sc.pml[i];
+        sw->pe[i] = sc.pe[i];
+      }
       sw->cur = cur;
-      sw->cF = cF;
-      sw->rec_terms = rec_terms;
-      sw->max_inner = max_inner;
+      sw->cF = ds.cF;
+      sw->rec_terms = ds.rec_terms;
+      sw->max_inner = ds.max_inner;
     }
     return 0;
   }
