@@ -371,6 +371,13 @@ def recover_kernel_work(n, nnz, wf, p, r, terms, outer_steps, b=8):
     return flops, bytes_
 
 
+def select_kernel_flops(n, nnz, m, evals):
+    """Algorithmic FP64 flops of one Algorithm 1 launch (an FMA counts 2): m sparse products (2 nnz), one
+    sum of squares per pass (2 n, m + 2 passes besides the evaluations), and per objective evaluation the
+    combination sum_k binom(m,k) z^(m-k) V_k (2 (m+1) n) and its sum of squares (2 n)."""
+    return m * 2 * nnz + (m + 2) * 2 * n + evals * (2 * (m + 1) * n + 2 * n)
+
+
 def select_kernel_bytes(n, nnz, m, r_guard, evals, b=8):
     """Algorithmic bytes of one Algorithm 1 launch: m sparse matrix-vector products (the guarded chain to
     r and the extension to m), each reading the operator ((4 + b) nnz + 4(n+1)) and one basis vector and
@@ -506,8 +513,8 @@ class SingleRun:
         self.prm = self.api.read_params(self.params)
         return statistics.mean(self.step_ms)
 
-    def kernels(self, hbm_peak):
-        """Per-kernel time in the step and share; Algorithm 1's kernel against HBM."""
+    def kernels(self, hbm_peak, roof=None):
+        """Per-kernel time in the step and share; Algorithm 1's kernel against the FP64 roof and HBM."""
         n, nnz = self.A.n, self.A.nnz
         out = {"select_kernel": {"ms": self.phase_ms[0]}}
         for idx, h in enumerate(HS):
@@ -522,9 +529,15 @@ class SingleRun:
             v["share"] = v["ms"] / tot if tot > 0 else None
         b = 8 if self.precision == "f64" else 4
         sb = select_kernel_bytes(n, nnz, 61, self.prm["r"], self.prm["evals"], b)
-        gbs = sb / (self.phase_ms[0] / 1000.0) / 1e9
-        out["select_kernel"].update({"evals": self.prm["evals"], "r": self.prm["r"], "bytes": sb,
+        sf = select_kernel_flops(n, nnz, 61, self.prm["evals"])
+        sel_s = self.phase_ms[0] / 1000.0
+        gbs = sb / sel_s / 1e9
+        out["select_kernel"].update({"evals": self.prm["evals"], "r": self.prm["r"], "bytes": sb, "flops": sf,
+                                     "fp64_gflops": sf / sel_s / 1e9,
+                                     "fp64_frac": (sf / sel_s / 1e9 / roof["gflops"]) if roof else None,
                                      "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                                     "bound": "alu (each objective pass is (m+1) FMAs per 8 (m+1) bytes, above "
+                                              "the FP64/HBM balance of a GB300)",
                                      "bytes_note": "m products ((4+b) nnz + 4(n+1) + 16n each), the rescaling "
                                                    "(16 n r) and one pass over V_0..V_m per objective "
                                                    "evaluation ((m+1) 8 n); of measured HBM"})
@@ -620,7 +633,7 @@ def run_single(args, rank, world, local_rank):
                        "step": "Algorithm 1 + Algorithm 3 at each h (2 solves)",
                        "l2": "flushed between steps (2 x L2 write, outside the step events); working set above L2",
                        "parallelism": f"replicas x{world}", **run.summary()},
-            "roofline": run.roofline(roof, hbm_peak), "kernels": run.kernels(hbm_peak),
+            "roofline": run.roofline(roof, hbm_peak), "kernels": run.kernels(hbm_peak, roof),
             "fp64_roof": roof, "gpu_launches": int(run.launches), "wall_s_timed_region": run.wall}
     if run.clocks:
         line["clocks"] = run.clocks
@@ -636,7 +649,7 @@ def run_single(args, rank, world, local_rank):
         W32 = [w.double().cpu().numpy() for w in c32.W]
         comp = {"value": solves_per_second(ms32, world), "unit": "solves/s", "ms_per_step": ms32, "dtype": "f32",
                 "tol": "2^-24", "workload": workload_label("f32"), **c32.summary(),
-                "roofline": c32.roofline(None, hbm_peak), "kernels": c32.kernels(hbm_peak),
+                "roofline": c32.roofline(None, hbm_peak), "kernels": c32.kernels(hbm_peak, roof),
                 "gpu_launches": int(c32.launches), "clocks": c32.clocks,
                 "errors": {f"h={HS[-1]:g} vs GPU FP64 (same step)": max(rel_errors(W32[-1], W_primary[-1]))}}
         line["fp32"] = comp
@@ -1331,6 +1344,7 @@ def run_lowrank(args, rank, world, local_rank):
     A = api.DeviceLowRank(torch.as_tensor(U_h).to(dev).contiguous(), torch.as_tensor(W_h).to(dev).contiguous())
     V = torch.as_tensor(V_h).to(dev)
     flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size, dtype=torch.uint8, device=dev)
+    roof_m = measure_fp64_roof(lib, capi, dev, local_rank)
 
     def step():
         P = api.select_params(A, tol=TOL)
@@ -1390,9 +1404,10 @@ def run_lowrank(args, rank, world, local_rank):
                 for x in st)
     achieved = flops / solve_s / 1e9
     roof = {"bound": "alu", "kernel": "lr_series_kernel + lr_recover_kernel (the two solves of a step)",
-            "achieved": achieved, "peak": FP64_DERIVED_GFLOPS, "unit": "FP64 GFLOP/s",
-            "frac": achieved / FP64_DERIVED_GFLOPS, "traffic": None,
-            "peak_note": "FP64 pipe: 2 FMA/clk/SM x 2 flop x 152 SMs x 2070 MHz; achieved counts (4 n k + 4 n) w "
+            "achieved": achieved, "peak": roof_m["gflops"], "unit": "FP64 GFLOP/s",
+            "frac": achieved / roof_m["gflops"], "traffic": None,
+            "peak_note": f"of measured: FP64 FMA rate of the probe kernel ({roof_m['fma_per_clk_per_sm']:.3f} "
+                         f"FMA/clk/SM at {roof_m['sm_mhz']:.0f} MHz); achieved counts (4 n k + 4 n) w "
                          "flops per series term and (4 n k + 3 n) w per recovery term, k = 2; the working set is "
                          "L2-resident",
             "taylor_terms_per_s": terms / solve_s}
