@@ -96,6 +96,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-companion", action="store_true", help="skip the FP32 companion of the default line")
     ap.add_argument("--sweep", action="store_true", help="advdiff2d-1024: h = 1e-5 .. 1e-1 in FP64 and FP32")
+    ap.add_argument("--function-operator", action="store_true",
+                    help="the step through the operator-function path (phic_fn_*, the library's CSR product as "
+                         "the function): Algorithm 1 on the host with device passes, Algorithm 3 as a CUDA graph")
     ap.add_argument("--workload", default="advdiff2d-1024",
                     choices=sorted(WORKLOADS) + ["batch512", "serve", "exprk-adr", "lowrank-m2"])
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "mixed"])
@@ -598,7 +601,78 @@ def main():
         return run_lowrank(args, rank, world, local_rank)
     if args.sweep:
         return run_sweep(args, rank, world, local_rank)
+    if args.function_operator:
+        return run_function_operator(args, rank, world, local_rank)
     return run_single(args, rank, world, local_rank)
+
+
+def run_function_operator(args, rank, world, local_rank):
+    """The default step with A given as a function (phic_fn_select_params + phic_fn_solve, the product by
+    phic_csr_apply): Algorithm 1 runs its products on the stream and its guard and Brent's method on the host;
+    each Algorithm 3 is one CUDA graph with conditional WHILE nodes.  Times per solve with CUDA events;
+    the graph's construction (stream capture and instantiation) is inside the timed region."""
+    import torch
+
+    from paper_2509_26475_gb300 import api, build, capi
+
+    if world > 1:
+        raise SystemExit("--function-operator runs on one GPU")
+    build.build()
+    lib = capi.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    A_h, V_h, alpha = workload()
+    dt = torch_dtype()
+    F = api.FunctionOperator.from_csr(api.DeviceCSR.from_host(A_h, device=dev, dtype=dt))
+    V = torch.as_tensor(V_h).to(dt).to(dev)
+    flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size, dtype=torch.uint8, device=dev)
+
+    def step(evs=None):
+        P = api.select_params(F, tol=TOL)
+        if evs is not None:
+            evs[1].record(stream)
+        sts = []
+        for idx, h in enumerate(HS):
+            sts.append(api.solve(F, V, t_of(h), alpha, TOL, P)[1])
+            if evs is not None:
+                evs[2 + idx].record(stream)
+        return P, sts
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    K = max(1, args.steps)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 + len(HS))] for _ in range(K)]
+    l0 = lib.phic_launch_count()
+    with ClockSampler(local_rank, None) as clk:
+        w0 = time.perf_counter()
+        for k in range(K):
+            flush.fill_(k & 255)
+            evs[k][0].record(stream)
+            P, sts = step(evs[k])
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - w0
+    st = [api.read_stats(x) for x in sts]
+    if any(x["status"] != 0 for x in st) or api.read_params(P)["status"] != 0:
+        raise SystemExit("function operator: a device status was reported; no number is reported")
+    ms = statistics.mean(e[0].elapsed_time(e[-1]) for e in evs)
+    sel_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    solve_ms = [statistics.mean(e[1 + i].elapsed_time(e[2 + i]) for e in evs) for i in range(len(HS))]
+    terms = [x["series_terms"] + x["recovery_terms"] for x in st]
+    line = {"metric": METRIC, "value": len(HS) * 1000.0 / ms, "unit": "solves/s", "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": PRECISION, "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME + " through the operator-function path (phic_fn_*, phic_csr_apply)",
+                       "select_ms": sel_ms, "solve_ms": solve_ms, "terms": terms,
+                       "us_per_term": [1000.0 * m / t for m, t in zip(solve_ms, terms)],
+                       "s_int": [x["s_int"] for x in st], "l2": "flushed between steps", "parallelism": "x1"},
+            "roofline": None, "gpu_launches": int(lib.phic_launch_count() - l0), "wall_s_timed_region": wall}
+    cs = clk.summary()
+    if cs:
+        line["clocks"] = cs
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_single(args, rank, world, local_rank):

@@ -103,13 +103,14 @@ typedef struct {
   int32_t op_slots;        /* its diagonals (DIA) or entries per row (ELL); 0 otherwise */
 } phic_stats;
 
-/* phic_stats.op_format.  The setup picks DIA (the values of at most 16 diagonals, row-aligned) when
+/* phic_stats.op_format.  For stored operators the setup picks DIA (the values of at most 16 diagonals, row-aligned) when
  * the stored diagonals are that few and fill the rows well, else ELL (a fixed number of slots per row,
  * at most 64) when n times the longest row fits the copy's room, else the entries in CSR order. */
 #define PHIC_OP_CSR 0
 #define PHIC_OP_ELL 1
 #define PHIC_OP_DIA 2
 #define PHIC_OP_LOWRANK 3
+#define PHIC_OP_FUNCTION 4 /* a phic_fn_op: products by the caller's function */
 
 /* Flags of phic_solve */
 #define PHIC_NO_V0 1u /* V holds v_1..v_p only (p rows); the result is sum_{j>=1} alpha_i^j phi_j(t_i A) v_j
@@ -232,6 +233,71 @@ phic_status phic_lowrank_solve(const phic_lowrank* A, int32_t p, int32_t r, cons
                                const double* alpha, double tol, const phic_params* params_dev, uint32_t flags,
                                int32_t max_terms, void* W, void* ws, size_t ws_bytes, phic_stats* stats_dev,
                                int32_t prec, phic_stream_t stream);
+
+/* ---- Operators given as functions ------------------------------------------------------------------
+ * Algorithms 1 and 3 need A only through products A X (Sections 3 and 4); here the caller supplies that
+ * product as a function, for operators that are not stored as a matrix (a stencil applied on the fly, a
+ * convolution, a composition of factors).  The function enqueues Y = A X on the stream it is given and
+ * returns; it must not synchronise or allocate.
+ *
+ * phic_fn_solve runs Algorithm 3 as one CUDA graph: the library records the caller's product into the
+ * graph once for each place it occurs (the series term, the first-block recovery, the recovery term), by
+ * stream capture, and every data-dependent loop of the method (the series' terms, the recovery's steps and
+ * each step's terms) is a conditional WHILE node whose condition the library's kernels set on the device,
+ * so that no Taylor term returns to the host.  The function is therefore called during the call to
+ * phic_fn_solve, on a capturing stream, and its work must be capturable (kernel launches, memsets and
+ * device-to-device copies on that stream only).
+ *
+ * phic_fn_select_params runs Algorithm 1 with the products enqueued directly on `stream` (in FP64), one
+ * per basis vector, and synchronises `stream` after each (the guard and Brent's method are evaluated on
+ * the host between device passes). */
+
+/* Y = A X for the columns 0..w-1 of an n-row block, on `stream`.  X and Y are device arrays of type prec
+ * (PHIC_F64 or PHIC_F32), row-major: X(i, c) at X[i ldx + c], Y(i, c) at Y[i ldy + c]; ldx, ldy >= w (in
+ * elements).  X and Y do not overlap.  Return 0 on success, non-zero to make the calling entry point fail
+ * with PHIC_CUDA_ERROR.  phic_fn_select_params calls it with prec = PHIC_F64 whatever the operator's
+ * precision. */
+typedef int32_t (*phic_apply_fn)(void* ctx, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t w,
+                                 int32_t prec, phic_stream_t stream);
+
+typedef struct {
+  int64_t n;
+  int32_t prec;          /* precision of the solve's tiles (PHIC_F64 or PHIC_F32) */
+  int32_t pad;
+  phic_apply_fn apply;
+  void* ctx;             /* passed to apply */
+  double norm_bound;     /* an upper bound of ||A||_inf (> 0): scales the Taylor terms so that
+                            ||(A - xi I) 2^-eA||_inf < 1, as the stored operators' own norms do */
+} phic_fn_op;
+
+/* Workspace bytes of phic_fn_select_params: the basis V_0..V_m (n (m+1) doubles) and per-chunk partials. */
+phic_status phic_fn_select_workspace_size(int64_t n, int32_t m, size_t* bytes);
+
+/* Algorithm 1 (Section 3) for a function operator: as phic_select_params, with the products of the
+ * power basis and its extension by A->apply (FP64).  Synchronises `stream` once per basis vector and once
+ * per objective evaluation; writes params_dev (device) on `stream` before returning. */
+phic_status phic_fn_select_params(const phic_fn_op* A, const phic_select_opts* opts, const double* v, void* ws,
+                                  size_t ws_bytes, phic_params* params_dev, phic_stream_t stream);
+
+/* Workspace bytes of phic_fn_solve: the tiles V, D, S and the product Y ((p+1) r columns each), G and E
+ * (2r columns; r when p = 0) and a control block. */
+phic_status phic_fn_solve_workspace_size(int64_t n, int32_t p, int32_t r, int32_t prec, size_t* bytes);
+
+/* Algorithm 3 (Section 4) for a function operator; arguments as phic_solve (prec must equal A->prec;
+ * flags 0 or PHIC_NO_V0).  Builds, instantiates and launches one CUDA graph on `stream` and releases it
+ * (the launch completes asynchronously; the graph is not kept).  The caller's apply is called three times
+ * during the call, on a capturing stream.  Returns PHIC_CUDA_ERROR when apply fails or its work cannot be
+ * captured. */
+phic_status phic_fn_solve(const phic_fn_op* A, int32_t p, int32_t r, const void* V, const double* t,
+                          const double* alpha, double tol, const phic_params* params_dev, uint32_t flags,
+                          int32_t max_terms, void* W, void* ws, size_t ws_bytes, phic_stats* stats_dev,
+                          int32_t prec, phic_stream_t stream);
+
+/* A CSR product in the form of phic_apply_fn (ctx: a const phic_csr* whose arrays are device memory and
+ * whose prec matches the call's prec for FP32 calls; FP64 calls on an FP32 CSR read its values as FP32 and
+ * compute in FP64).  An example of the interface, and the product the tests compare the function path with. */
+int32_t phic_csr_apply(void* ctx, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t w, int32_t prec,
+                       phic_stream_t stream);
 
 /* ---- Batched solves -------------------------------------------------------------------------------
  * Many independent instances (each its own A, p, r, t, alpha, tol and precision) in ONE persistent
@@ -506,8 +572,8 @@ int32_t phic_version(void);
 /* Sizes in bytes of the public structs, so that a binding can check its layouts: out[i] for i < n (in
  * this order: phic_csr, phic_select_opts, phic_params, phic_stats, phic_lowrank, phic_batch_item,
  * phic_batch_config, phic_batch_info, phic_server_config, phic_operator, phic_request,
- * phic_request_info, phic_server_counters).  Returns how many there are (13), whatever n is; out may be
- * NULL when n is 0. */
+ * phic_request_info, phic_server_counters, phic_fn_op).  Returns how many there are (14), whatever n is;
+ * out may be NULL when n is 0. */
 int32_t phic_struct_sizes(size_t* out, int32_t n);
 
 #ifdef __cplusplus

@@ -127,7 +127,7 @@ def read_stats(stats: torch.Tensor) -> dict:
     s = capi.phic_stats.from_buffer_copy(raw)
     return dict(status=s.status, s_int=s.s_int, series_terms=s.series_terms, max_inner_terms=s.max_inner_terms,
                 recovery_terms=s.recovery_terms, spmm_count=s.spmm_count, xi=s.xi, s=s.s,
-                op_format=("csr", "ell", "dia", "lowrank")[s.op_format] if 0 <= s.op_format <= 3 else s.op_format,
+                op_format=("csr", "ell", "dia", "lowrank", "function")[s.op_format] if 0 <= s.op_format <= 4 else s.op_format,
                 op_slots=s.op_slots)
 
 
@@ -142,10 +142,15 @@ def select_params(A: DeviceCSR, m: int = 61, tol: float = 2.0**-53, delta: float
     lib.phic_select_opts_default(ctypes.byref(opts))
     opts.m, opts.tol, opts.delta, opts.seed, opts.max_evals = int(m), float(tol), float(delta), int(seed) & (2**64 - 1), int(max_evals)
     lowrank = isinstance(A, DeviceLowRank)
+    fnop = isinstance(A, FunctionOperator)
     if lowrank:
         out_sz = ctypes.c_size_t(0)
         capi.check(lib.phic_lowrank_select_workspace_size(A.n, A.k, int(m), ctypes.byref(out_sz)),
                    "phic_lowrank_select_workspace_size")
+        nbytes = int(out_sz.value)
+    elif fnop:
+        out_sz = ctypes.c_size_t(0)
+        capi.check(lib.phic_fn_select_workspace_size(A.n, int(m), ctypes.byref(out_sz)), "phic_fn_select_workspace_size")
         nbytes = int(out_sz.value)
     else:
         nbytes = select_workspace_bytes(A.n, m)
@@ -156,7 +161,7 @@ def select_params(A: DeviceCSR, m: int = 61, tol: float = 2.0**-53, delta: float
             raise ValueError("v must be a contiguous CUDA float64 tensor with n entries")
         vptr = v.data_ptr()
     c = A.struct()
-    fn = lib.phic_lowrank_select_params if lowrank else lib.phic_select_params
+    fn = lib.phic_lowrank_select_params if lowrank else lib.phic_fn_select_params if fnop else lib.phic_select_params
     st = fn(ctypes.byref(c), ctypes.byref(opts), vptr, ws.data_ptr(), ws.numel(), params.data_ptr(),
             _stream_handle(stream))
     capi.check(st, "phic_select_params")
@@ -197,16 +202,22 @@ def solve(A: DeviceCSR, V: torch.Tensor, t, alpha, tol: float, params: torch.Ten
         raise ValueError("out has the wrong shape or dtype")
     stats = stats if stats is not None else new_stats(dev)
     lowrank = isinstance(A, DeviceLowRank)
+    fnop = isinstance(A, FunctionOperator)
     if lowrank:
         out_sz = ctypes.c_size_t(0)
         capi.check(lib.phic_lowrank_solve_workspace_size(A.n, A.k, int(p), int(r), int(prec), ctypes.byref(out_sz)),
                    "phic_lowrank_solve_workspace_size")
         nbytes = int(out_sz.value)
+    elif fnop:
+        out_sz = ctypes.c_size_t(0)
+        capi.check(lib.phic_fn_solve_workspace_size(A.n, int(p), int(r), int(prec), ctypes.byref(out_sz)),
+                   "phic_fn_solve_workspace_size")
+        nbytes = int(out_sz.value)
     else:
         nbytes = solve_workspace_bytes(A.n, A.nnz, p, r, prec)
-    ws = workspace if workspace is not None else workspaces.get(("solve", prec), nbytes, dev)
+    ws = workspace if workspace is not None else workspaces.get(("fn" if fnop else "solve", prec), nbytes, dev)
     c = A.struct()
-    fn = lib.phic_lowrank_solve if lowrank else lib.phic_solve
+    fn = lib.phic_lowrank_solve if lowrank else lib.phic_fn_solve if fnop else lib.phic_solve
     st = fn(ctypes.byref(c), int(p), int(r), V.data_ptr(), t.ctypes.data, alpha.ctypes.data, float(tol),
             params.data_ptr(), int(flags), int(max_terms), W.data_ptr(), ws.data_ptr(), ws.numel(),
             stats.data_ptr(), int(prec), _stream_handle(stream))
@@ -614,3 +625,88 @@ class DeviceLowRank:
     @property
     def rowptr(self):  # device of the operator, for the helpers that allocate next to it
         return self.U
+
+
+class FunctionOperator:
+    """An operator given by its product Y = A X (the phic_fn_* entry points): accepted by select_params and
+    solve in place of a DeviceCSR.  ``apply`` is either a C function pointer of type phic_apply_fn (an int,
+    e.g. ``ctypes.cast(lib.phic_csr_apply, c_void_p).value``, with ``ctx`` its context pointer) or a Python
+    callable ``apply(X, Y, w, prec, stream)`` that receives X (n, ldx) and Y (n, ldy) as CUDA tensor views
+    over the library's buffers (their first w columns are the block) and a torch stream, and enqueues
+    Y[:, :w] = A X[:, :w] on that stream without allocating or synchronising (solve calls it while the
+    library captures a CUDA graph).  ``norm_bound`` bounds ||A||_inf from above."""
+
+    def __init__(self, n: int, apply, norm_bound: float, dtype=torch.float64, ctx: int | None = None):
+        self.n = int(n)
+        self.dtype = dtype
+        self.norm_bound = float(norm_bound)
+        self._keep = []
+        if callable(apply) and not isinstance(apply, int):
+            user = apply
+
+            def trampoline(_ctx, X, ldx, Y, ldy, w, prec, stream):
+                try:
+                    dt = _TORCH_DT[int(prec)]
+                    Xt = _device_view(X, self.n, int(ldx), dt)
+                    Yt = _device_view(Y, self.n, int(ldy), dt)
+                    s = torch.cuda.ExternalStream(int(stream)) if stream else torch.cuda.current_stream()
+                    with torch.cuda.stream(s):
+                        user(Xt, Yt, int(w), int(prec), s)
+                    return 0
+                except Exception:  # the library reports a failed product as PHIC_CUDA_ERROR
+                    import traceback
+
+                    traceback.print_exc()
+                    return 1
+
+            cfn = capi.APPLY_FN(trampoline)
+            self._keep.append(cfn)
+            self._fnptr = ctypes.cast(cfn, ctypes.c_void_p).value
+            self._ctx = None
+        else:
+            self._fnptr = int(apply)
+            self._ctx = ctx
+
+    @classmethod
+    def from_csr(cls, A: "DeviceCSR") -> "FunctionOperator":
+        """The library's own CSR product as the function (phic_csr_apply); the bound is ||A||_inf."""
+        lib = capi.load()
+        csr = A.struct()
+        vals = A.values.double() if A.values.dtype != torch.float64 else A.values
+        rows = torch.repeat_interleave(torch.arange(A.n, device=vals.device), A.rowptr[1:] - A.rowptr[:-1])
+        bound = float(torch.zeros(A.n, dtype=torch.float64, device=vals.device).index_add_(0, rows, vals.abs()).max())
+        op = cls(A.n, ctypes.cast(lib.phic_csr_apply, ctypes.c_void_p).value, bound, A.values.dtype,
+                 ctypes.addressof(csr))
+        op._keep += [csr, A]
+        return op
+
+    @property
+    def prec(self) -> int:
+        return prec_of(self.dtype)
+
+    @property
+    def nnz(self) -> int:
+        return 0
+
+    @property
+    def rowptr(self):  # the device the operator lives on, as DeviceCSR exposes it
+        return torch.empty(0, device="cuda")
+
+    def struct(self) -> capi.phic_fn_op:
+        c = capi.phic_fn_op(self.n, self.prec, 0, self._fnptr, self._ctx, self.norm_bound)
+        self._keep.append(c)
+        return c
+
+
+class _CudaArray:
+    """A CUDA array interface over a raw device pointer (no copy), for torch.as_tensor."""
+
+    def __init__(self, ptr: int, shape, strides_bytes, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "strides": tuple(strides_bytes), "version": 3}
+
+
+def _device_view(ptr: int, n: int, ld: int, dtype) -> torch.Tensor:
+    es = 8 if dtype == torch.float64 else 4
+    typestr = "<f8" if dtype == torch.float64 else "<f4"
+    return torch.as_tensor(_CudaArray(ptr, (n, ld), (ld * es, es), typestr), device="cuda")

@@ -109,9 +109,20 @@ class phic_server_counters(ctypes.Structure):
                 ("failed", ctypes.c_int64), ("slices", ctypes.c_int64), ("max_slice_requests", ctypes.c_int64),
                 ("arena_in_use", ctypes.c_int64), ("arena_peak", ctypes.c_int64), ("gpu_busy_ms", ctypes.c_double)]
 
+# phic_apply_fn: Y = A X on a stream (see include/phicomb.h)
+APPLY_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                            ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p)
+
+
+class phic_fn_op(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("prec", ctypes.c_int32), ("pad", ctypes.c_int32), ("apply", ctypes.c_void_p),
+                ("ctx", ctypes.c_void_p), ("norm_bound", ctypes.c_double)]
+
+
 # The public structs in the order phic_struct_sizes reports them.
 STRUCTS = (phic_csr, phic_select_opts, phic_params, phic_stats, phic_lowrank, phic_batch_item, phic_batch_config,
-           phic_batch_info, phic_server_config, phic_operator, phic_request, phic_request_info, phic_server_counters)
+           phic_batch_info, phic_server_config, phic_operator, phic_request, phic_request_info, phic_server_counters,
+           phic_fn_op)
 
 
 PHIC_REQ_QUEUED, PHIC_REQ_LOADING, PHIC_REQ_RUNNING, PHIC_REQ_COPYING, PHIC_REQ_DONE = range(5)
@@ -175,6 +186,15 @@ SIGNATURES = [
     ("phic_set_spin_limit_ms", None, [ctypes.c_double]),
     ("phic_set_blocks_per_sm", None, [ctypes.c_int32]),
     ("phic_set_test_fault", None, [ctypes.c_int32]),
+    ("phic_fn_select_workspace_size", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    ("phic_fn_select_params", ctypes.c_int, [ctypes.POINTER(phic_fn_op), ctypes.POINTER(phic_select_opts), _P, _P,
+                                             ctypes.c_size_t, _P, _P]),
+    ("phic_fn_solve_workspace_size", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                    ctypes.POINTER(ctypes.c_size_t)]),
+    ("phic_fn_solve", ctypes.c_int, [ctypes.POINTER(phic_fn_op), ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
+                                     ctypes.c_double, _P, ctypes.c_uint32, ctypes.c_int32, _P, _P, ctypes.c_size_t, _P,
+                                     ctypes.c_int32, _P]),
+    ("phic_csr_apply", ctypes.c_int32, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]),
     ("phic_probe_fp64_fma", ctypes.c_int, [ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int64), _P]),
     ("phic_test_objective_coeffs", ctypes.c_int, [ctypes.c_int32, ctypes.c_double, _P, _P]),
     ("phic_status_string", ctypes.c_char_p, [ctypes.c_int32]),

@@ -137,7 +137,7 @@ int32_t phic_struct_sizes(size_t* out, int32_t n) {
                           sizeof(phic_stats),         sizeof(phic_lowrank),      sizeof(phic_batch_item),
                           sizeof(phic_batch_config),  sizeof(phic_batch_info),   sizeof(phic_server_config),
                           sizeof(phic_operator),      sizeof(phic_request),      sizeof(phic_request_info),
-                          sizeof(phic_server_counters)};
+                          sizeof(phic_server_counters), sizeof(phic_fn_op)};
   const int32_t count = (int32_t)(sizeof(sizes) / sizeof(sizes[0]));
   for (int32_t i = 0; out && i < n && i < count; ++i) out[i] = sizes[i];
   return count;

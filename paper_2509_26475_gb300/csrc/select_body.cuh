@@ -42,7 +42,7 @@ struct BrentSM {
   int evals, max_evals, started, done;
 };
 
-__device__ void brent_start(BrentSM& b, double lo, double hi, double tabs, int max_evals) {
+__host__ __device__ void brent_start(BrentSM& b, double lo, double hi, double tabs, int max_evals) {
   const double golden = 0.38196601125010515;  // (3 - sqrt 5)/2
   b.lo = lo;
   b.hi = hi;
@@ -56,7 +56,7 @@ __device__ void brent_start(BrentSM& b, double lo, double hi, double tabs, int m
   b.u = lo + golden * (hi - lo);
 }
 
-__device__ void brent_feed(BrentSM& b, double fu) {
+__host__ __device__ void brent_feed(BrentSM& b, double fu) {
   const double golden = 0.38196601125010515;
   const double sqrt_eps = 1.4901161193847656e-08;  // sqrt(2^-52)
   b.evals += 1;
