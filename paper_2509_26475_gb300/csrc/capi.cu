@@ -78,7 +78,7 @@ phic_status phic_solve_workspace_size(int64_t n, int64_t nnz, int32_t p, int32_t
   if (!bytes || n < 1 || n >= (int64_t)INT32_MAX || nnz < 0 || nnz >= (int64_t)INT32_MAX || p < 0 ||
       p > PHIC_MAX_P || r < 1 || r > PHIC_MAX_R || (p + 1) * r > PHIC_MAX_WIDTH || (prec != PHIC_F64 && prec != PHIC_F32))
     return PHIC_INVALID_ARG;
-  *bytes = solve_layout(n, nnz, p, r, prec).total;
+  *bytes = solve_layout(n, nnz, p, r, prec, true).total;
   return PHIC_OK;
 }
 
@@ -93,7 +93,7 @@ phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, c
     run_series = (flags & PHIC_PHASE_SERIES) != 0;
     run_recover = (flags & PHIC_PHASE_RECOVER) != 0;
   }
-  const SolveLayout L = solve_layout(A->n, A->nnz, p, r, prec);
+  const SolveLayout L = solve_layout(A->n, A->nnz, p, r, prec, true);
   if (ws_bytes < L.total) return PHIC_WORKSPACE_TOO_SMALL;
   char* base = static_cast<char*>(ws);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -180,7 +180,7 @@ extern "C" phic_status phic_solve_noalloc(const phic_csr* A, int32_t p, int32_t 
                                           uint32_t flags, int32_t max_terms, void* W, phic_stats* stats_dev,
                                           int32_t prec, phic_stream_t stream) {
   if (!solve_args_ok(A, p, r, V, t, alpha, tol, flags, PHIC_NO_V0, prec) || !W || !params_dev) return PHIC_INVALID_ARG;
-  const SolveLayout L = solve_layout(A->n, A->nnz, p, r, prec);
+  const SolveLayout L = solve_layout(A->n, A->nnz, p, r, prec, true);
   if (L.total > (size_t)PHIC_NOALLOC_MAX_BYTES) return PHIC_WORKSPACE_TOO_SMALL;
   void* scratch = nullptr;
   if (noalloc_scratch(&scratch) != cudaSuccess) return PHIC_CUDA_ERROR;

@@ -15,7 +15,9 @@ struct Ctl;
 struct TileLayout {
   int w, ws, cw, L, Lp2;
 };
-TileLayout pick_layout(int w, int elem_bytes);
+// odd_cw: FP64 tiles may also take 3 or 5 columns a lane where that leaves fewer idle lanes (only the
+// single-instance series kernels are built for those widths).
+TileLayout pick_layout(int w, int elem_bytes, bool odd_cw = false);
 
 // Per-solve loop state in device memory.  The series writes the first block; the recovery reads it and,
 // when it stops between outer steps (a bounded slice of a batched launch), records where to resume.

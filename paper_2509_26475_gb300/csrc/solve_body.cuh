@@ -920,7 +920,8 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
 #pragma unroll
           for (int j = 0; j < CW; ++j) acc[j] = fma(xiB, own[j], acc[j]);
         }
-        T vo[CW], sv[CW], vn[CW], dn[CW], vp[CW];
+        T vo[CW], sv[CW], vn[CW], dn[CW];
+        [[maybe_unused]] T vp[CW];
         VecIO<T, CW>::ld(Vo + o, vo);
         VecIO<T, CW>::ld(S + o, sv);
         // block b-1 of the old V, for the columns of blocks b >= 2.  FP32 tiles take it as one vector when r
