@@ -303,23 +303,27 @@ struct VecIO<double, 4> {
     reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
   }
 };
-// Three and five doubles a lane (FP64 series tiles whose width is a multiple of 3 or 5, so that a row
-// needs no idle lanes): 24- and 40-byte chunks are only 8-byte aligned, so they move one element at a time.
-template <int CW>
+// Three and five values a lane (series tiles whose width is a multiple of 3 or 5, so that a row needs no
+// idle lanes): such chunks are aligned to one element only, so they move one element at a time.
+template <typename T, int CW>
 struct VecIOScalar {
-  static __device__ __forceinline__ void ld(const double* p, double (&x)[CW]) {
+  static __device__ __forceinline__ void ld(const T* p, T (&x)[CW]) {
 #pragma unroll
     for (int j = 0; j < CW; ++j) x[j] = p[j];
   }
-  static __device__ __forceinline__ void st(double* p, const double (&x)[CW]) {
+  static __device__ __forceinline__ void st(T* p, const T (&x)[CW]) {
 #pragma unroll
     for (int j = 0; j < CW; ++j) p[j] = x[j];
   }
 };
 template <>
-struct VecIO<double, 3> : VecIOScalar<3> {};
+struct VecIO<double, 3> : VecIOScalar<double, 3> {};
 template <>
-struct VecIO<double, 5> : VecIOScalar<5> {};
+struct VecIO<double, 5> : VecIOScalar<double, 5> {};
+template <>
+struct VecIO<float, 3> : VecIOScalar<float, 3> {};
+template <>
+struct VecIO<float, 5> : VecIOScalar<float, 5> {};
 template <>
 struct VecIO<float, 1> {
   static __device__ __forceinline__ void ld(const float* p, float (&x)[1]) { x[0] = *p; }

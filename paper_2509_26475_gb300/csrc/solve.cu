@@ -33,12 +33,16 @@ namespace {
 #ifndef PHIC_SERIES_MINB_ODD_F64
 #define PHIC_SERIES_MINB_ODD_F64 2
 #endif
+#ifndef PHIC_SERIES_MINB_F32_CW5
+#define PHIC_SERIES_MINB_F32_CW5 3
+#endif
 template <typename T, int CW, bool kWide>
 constexpr int series_minb() {
   return !kWide ? 2
-         : (sizeof(T) == 4 && CW <= 4) ? PHIC_SERIES_MINB_F32
-         : (CW == 3 || CW == 5)        ? PHIC_SERIES_MINB_ODD_F64
-                                       : wide_minb<T>();
+         : (sizeof(T) == 4 && CW <= 4)     ? PHIC_SERIES_MINB_F32
+         : (sizeof(T) == 4 && CW == 5)     ? PHIC_SERIES_MINB_F32_CW5
+         : (CW == 3 || CW == 5)            ? PHIC_SERIES_MINB_ODD_F64
+                                           : wide_minb<T>();
 }
 
 template <typename T, bool kWide>
@@ -56,7 +60,7 @@ cudaError_t dispatch_series_b(const SolveArgs& a, cudaStream_t st, int* g) {
 #endif
     case 3:
     case 5:
-      if constexpr (sizeof(T) == 8 && kWide) {
+      if constexpr (kWide) {
         if (a.S_lay.cw == 3) return coop_launch(series_kernel<T, 3, series_minb<T, 3, kWide>()>, items, bps, a, st, g);
         return coop_launch(series_kernel<T, 5, series_minb<T, 5, kWide>()>, items, bps, a, st, g);
       }
@@ -104,6 +108,9 @@ cudaError_t launch_series(const SolveArgs& a, int prec, cudaStream_t st, int* gr
 #define PHIC_WIDE_CW4_F64 8
 #endif
 
+#ifndef PHIC_ODD_CW_F32
+#define PHIC_ODD_CW_F32 1
+#endif
 TileLayout pick_layout(int w, int elem_bytes, bool odd_cw) {
   const int wp = (PHIC_PAD_ODD && w >= 3 && w < 32 && (w & 1)) ? w + 1 : w;
   const int cw_max = elem_bytes == 4 ? PHIC_CW_MAX_F32 : (wp >= PHIC_WIDE_CW4_F64 && wp % 4 == 0 ? 4 : PHIC_CW_MAX);
@@ -128,10 +135,11 @@ TileLayout pick_layout(int w, int elem_bytes, bool odd_cw) {
   t.L = t.ws / t.cw;
   t.Lp2 = 1;
   while (t.Lp2 < t.L) t.Lp2 <<= 1;
-  // FP64 lanes cost a full FP64 instruction whether their columns are live or not (the lanes of a row
-  // are padded to a power of two): where 3 or 5 columns a lane fill a row's lanes better, take them.
-  // The 1024^2 series, 20 columns: 4 columns a lane use 8 lanes for 5 live ones, 5 a lane use 4 of 4.
-  if (odd_cw && elem_bytes == 8 && w > 4) {
+  // The lanes of a row are padded to a power of two, and an idle lane costs its warp's instructions all
+  // the same (in FP64 a whole FP64 instruction): where 3 or 5 columns a lane fill a row's lanes better,
+  // take them.  The 1024^2 series, 20 columns: 4 columns a lane use 8 lanes for 5 live ones, 5 a lane use
+  // 4 of 4 (GB300, 54 terms: FP64 29.8 -> 20.0 ms; FP32 at 28 terms 4.55 -> 4.15 ms).
+  if (odd_cw && (elem_bytes == 8 || PHIC_ODD_CW_F32) && w > 4) {
     for (const int cw : {5, 3}) {
       if (w % cw != 0 || w / cw > 32) continue;
       int lp2 = 1;

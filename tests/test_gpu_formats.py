@@ -1,7 +1,7 @@
 """Every copy format of B the setup can pick (DIA with 5, 7 or another number of diagonals, ELL, CSR
 order), each with its own loop nest in the single-instance kernels, against the oracle in FP64 (bar
 1e-12 at tol 2^-53) and in FP32 (bar 5e-6 at tol 2^-24, against the FP64 oracle), for block widths
-that take every lane chunk (1, 2, 4 and 8 columns, and in FP64 3 and 5: widths 12 and 20).  phic_stats reports the format the solve used.
+that take every lane chunk (1, 2, 4 and 8 columns, and 3 and 5: widths 12 and 20).  phic_stats reports the format the solve used.
 Both precisions run with the oracle's (s, xi), so that s_int >= 2 and the recovery loop runs."""
 import numpy as np
 import pytest

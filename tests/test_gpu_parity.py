@@ -94,7 +94,7 @@ def test_nonnormal_dense_block(oracle_mod):
 @pytest.mark.parametrize("p,r", [(0, 1), (0, 3), (1, 2), (2, 1), (4, 3), (6, 5), (7, 16), (15, 8), (0, 5), (2, 2),
                                  (7, 3), (1, 5)])
 def test_widths_and_padding(oracle_mod, p, r):
-    """Block widths (p+1) r from 1 to 128, odd and padded layouts; FP64 widths 5, 6, 10, 24 and 35 take the
+    """Block widths (p+1) r from 1 to 128, odd and padded layouts; widths 5, 6, 10, 24 and 35 take the
     series kernels with 3 or 5 columns a lane."""
     Acsr = wl.convection_diffusion(29, 2, 5.0)
     rng = np.random.default_rng(100 * p + r)
