@@ -570,7 +570,9 @@ class SingleRun:
                                  "frac_of_measured": hbm_gbs / hbm_peak}}
         return {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
                 **common, "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, of measured); algorithmic bytes "
-                                       "(4+b) nnz + 4(n+1) + 4 n 2r b per Taylor term"}
+                                       "(4+b) nnz + 4(n+1) + 4 n 2r b per Taylor term, which count every tile "
+                                       "pass as DRAM traffic: a fraction above 1 means L2 and shared memory "
+                                       "hold part of them (compare `traffic`, the DRAM bytes ncu measured)"}
 
     def summary(self):
         return {"s": self.prm["s"], "xi": self.prm["xi"], "s_int": [x["s_int"] for x in self.sts],

@@ -364,6 +364,30 @@ struct VecIO<float, 8> {
   }
 };
 
+// Loads and stores of the workspace tiles, which are always in global memory.  An FP32 lane's 32-byte
+// chunk (8 floats) moves as one 256-bit access (sm_100 and later) instead of two 128-bit ones: the
+// 1024^2 FP32 recovery, latency-bound on L2, went 86.1 -> 74.3 ms for 2882 terms on GB300.  The same for
+// 4-double chunks measured 1.3 % slower on the FP64 recovery (bound by the FP64 pipe), so FP64 keeps
+// VecIO.  The chunks are 32-byte aligned: tiles start on 256-byte boundaries and their row strides and
+// chunk offsets are multiples of the chunk.  Plain (coherent) accesses: the tiles are rewritten between
+// the terms of one launch.  Volatile, so that no load is merged with or moved across another access of
+// the same kind; E, which may live in shared memory, keeps VecIO.
+template <typename T, int CW>
+struct VecIOG : VecIO<T, CW> {};
+template <>
+struct VecIOG<float, 8> {
+  static __device__ __forceinline__ void ld(const float* p, float (&x)[8]) {
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+                 : "l"(p));
+  }
+  static __device__ __forceinline__ void st(float* p, const float (&x)[8]) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "l"(p), "f"(x[0]), "f"(x[1]), "f"(x[2]), "f"(x[3]), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7])
+                 : "memory");
+  }
+};
+
 // Sum over the lanes of one row group (Lp2 consecutive lanes, a power of two <= 32, aligned).
 template <typename T>
 __device__ __forceinline__ T group_sum(T v, int Lp2) {

@@ -199,7 +199,7 @@ __device__ __forceinline__ void spmm_ent(const int* __restrict__ rowptr, const C
     T x[U][CW];
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (u < cnt) VecIO<T, CW>::ld(X + (size_t)e[u].col * ws + c0, x[u]);
+      if (u < cnt) VecIOG<T, CW>::ld(X + (size_t)e[u].col * ws + c0, x[u]);
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (u < cnt) {
@@ -229,7 +229,7 @@ __device__ __forceinline__ void spmm_ell_dyn(const CsrEnt<T>* __restrict__ ent, 
     T x[U][CW];
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (q0 + u < K) VecIO<T, CW>::ld(X + (size_t)e[u].col * ws + c0, x[u]);
+      if (q0 + u < K) VecIOG<T, CW>::ld(X + (size_t)e[u].col * ws + c0, x[u]);
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (q0 + u < K) {
@@ -255,7 +255,7 @@ __device__ __forceinline__ void spmm_dia_k(const T* __restrict__ val, const int 
     const int j = row + off[d];
     const int jj = (unsigned)j < (unsigned)n ? j : row;
     v[d] = val[(size_t)d * n + row];
-    VecIO<T, CW>::ld(X + (size_t)jj * ws + c0, x[d]);
+    VecIOG<T, CW>::ld(X + (size_t)jj * ws + c0, x[d]);
   }
   DotAcc<T> acc_d[CW];
 #pragma unroll
@@ -279,7 +279,7 @@ __device__ __forceinline__ void spmm_dia_dyn(const T* __restrict__ val, const in
     const int jj = (unsigned)j < (unsigned)n ? j : row;
     const T v = val[(size_t)d * n + row];
     T x[CW];
-    VecIO<T, CW>::ld(X + (size_t)jj * ws + c0, x);
+    VecIOG<T, CW>::ld(X + (size_t)jj * ws + c0, x);
 #pragma unroll
     for (int c = 0; c < CW; ++c) acc_d[c].add(v, x[c]);
   }
@@ -807,9 +807,9 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
           part += fabs(x[j]);
         }
         const size_t o = (size_t)row * L.ws + c0;
-        VecIO<T, CW>::st(V1 + o, x);
-        VecIO<T, CW>::st(D1 + o, x);
-        VecIO<T, CW>::st(S + o, x);
+        VecIOG<T, CW>::st(V1 + o, x);
+        VecIOG<T, CW>::st(D1 + o, x);
+        VecIOG<T, CW>::st(S + o, x);
       }
       const T rs = group_sum(part, L.Lp2);
       if (act && lane == 0) umax(mx, (double)rs);
@@ -916,14 +916,14 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
         }
         if (nodiag && (LR || rowflag[row])) {  // no stored diagonal: apply the shift explicitly
           T own[CW];
-          VecIO<T, CW>::ld(Do + o, own);
+          VecIOG<T, CW>::ld(Do + o, own);
 #pragma unroll
           for (int j = 0; j < CW; ++j) acc[j] = fma(xiB, own[j], acc[j]);
         }
         T vo[CW], sv[CW], vn[CW], dn[CW];
         [[maybe_unused]] T vp[CW];
-        VecIO<T, CW>::ld(Vo + o, vo);
-        VecIO<T, CW>::ld(S + o, sv);
+        VecIOG<T, CW>::ld(Vo + o, vo);
+        VecIOG<T, CW>::ld(S + o, sv);
         // block b-1 of the old V, for the columns of blocks b >= 2.  FP32 tiles take it as one vector when r
         // is a multiple of the lane's width (the lane's columns then lie in one block and c0 - r is aligned),
         // which measured 9 % faster on the series; FP64 tiles read it per column in the update below (the
@@ -932,7 +932,7 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
 #pragma unroll
           for (int j = 0; j < CW; ++j) vp[j] = T(0);
           if (up_vec) {
-            if (kUp[0]) VecIO<T, CW>::ld(Vo + o - r, vp);
+            if (kUp[0]) VecIOG<T, CW>::ld(Vo + o - r, vp);
           } else {
 #pragma unroll
             for (int j = 0; j < CW; ++j)
@@ -956,9 +956,9 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
           pD += norm_piece(dn[j], bias, fscale, nf);
           pS += norm_piece(sv[j], bias, fscale, nf);
         }
-        VecIO<T, CW>::st(Vn + o, vn);
-        VecIO<T, CW>::st(Dn + o, dn);
-        VecIO<T, CW>::st(S + o, sv);
+        VecIOG<T, CW>::st(Vn + o, vn);
+        VecIOG<T, CW>::st(Dn + o, dn);
+        VecIOG<T, CW>::st(S + o, sv);
         nf |= row_nonfinite<T>(pD, pS);
       }
       const float rD = group_sum(pD, L.Lp2), rS = group_sum(pS, L.Lp2);
@@ -1313,7 +1313,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
           f[j] = v;
           part += fabs(v);
         }
-        VecIO<T, CW>::st(F + (size_t)row * L.ws + c0, f);
+        VecIOG<T, CW>::st(F + (size_t)row * L.ws + c0, f);
       }
       const T rs = group_sum(part, L.Lp2);
       if (act && lane == 0) umax(mx, (double)rs);
@@ -1444,7 +1444,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
           T e[CW];
           if (kk == 1 || shift_row) {
             T own[CW];
-            VecIO<T, CW>::ld(Go + o, own);
+            VecIOG<T, CW>::ld(Go + o, own);
             if (shift_row) {
 #pragma unroll
               for (int j = 0; j < CW; ++j) acc[j] = fma(xiB, own[j], acc[j]);
@@ -1462,7 +1462,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
             pF += kF[j] * norm_piece(acc[j], bias, fscale, nf);
             pE += norm_piece(e[j], bias, fscale, nf);
           }
-          VecIO<T, CW>::st(Gn + o, acc);
+          VecIOG<T, CW>::st(Gn + o, acc);
           VecIO<T, CW>::st(E + o, e);
           nf |= row_nonfinite<T>(pF, pE);
         }
@@ -1525,7 +1525,7 @@ __device__ __forceinline__ int recover_body(const SolveArgs& a, Team& tm, Recove
             e[j] = col_live(j) ? v : T(0);
             part += fabs(e[j]);
           }
-          VecIO<T, CW>::st(F + o, e);
+          VecIOG<T, CW>::st(F + o, e);
         }
         const T rs = group_sum(part, L.Lp2);
         if (act && lane == 0) umax(mx, (double)rs);
