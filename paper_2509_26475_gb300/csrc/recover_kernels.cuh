@@ -67,12 +67,24 @@ size_t e_smem_bytes(K kernel, const SolveArgs& a, size_t elem, int b) {
   return bytes;
 }
 
-// Tiles up to 4 columns: the 2-block kernel.  Wider tiles: the wide_minb kernel with E in shared
+// Resident blocks per SM of the recovery kernel for tiles wider than 4 columns.  FP64: wide_minb (3).
+// FP32: 2, with 128 registers: at 3 blocks (80 registers) the loop nest reloaded spilled state from
+// local memory, 2.5 loads a warp-row that missed L1 (shared memory holds E there); at 2 blocks the
+// 1024^2 recovery (E in shared memory either way) runs 2882 terms in 58.5 against 74.7 ms on GB300.
+#ifndef PHIC_RECOVER_MINB_F32
+#define PHIC_RECOVER_MINB_F32 2
+#endif
+template <typename T>
+constexpr int recover_wide_minb() {
+  return sizeof(T) == 4 ? PHIC_RECOVER_MINB_F32 : wide_minb<T>();
+}
+
+// Tiles up to 4 columns: the 2-block kernel.  Wider tiles: the recover_wide_minb kernel with E in shared
 // memory if it fits at that residency, else the 2-block kernel (128 registers) at 2 blocks per SM with
-// E in shared memory if it fits there, else the wide_minb kernel with E in the workspace.
+// E in shared memory if it fits there, else the recover_wide_minb kernel with E in the workspace.
 template <typename T, int CW>
 cudaError_t launch_recover_cw(const SolveArgs& a, cudaStream_t st, int* g) {
-  constexpr int WB = wide_minb<T>();
+  constexpr int WB = recover_wide_minb<T>();
   const long long items = (long long)a.n * a.F_lay.Lp2;
   const int cap = blocks_per_sm(sizeof(T));
   auto k2 = recover_kernel<T, CW, 2>;
