@@ -873,12 +873,16 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
     const int kk = lc.k;
     const int ph = phase++;
     slot_reset(tm, ph);
-    T kD[CW], kA[CW], kT[CW];
+    // this term's column coefficients: FP32 tiles keep them in registers; FP64 tiles read them from shared
+    // memory where they are used (3 CW registers fewer across the product; see the V update)
+    [[maybe_unused]] T kD[CW], kA[CW], kT[CW];
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int j = 0; j < CW; ++j) {
-      kD[j] = tk.kd[kI[j]];
-      kA[j] = tk.ka[kI[j]];
-      kT[j] = tk.kt[kI[j]];
+      for (int j = 0; j < CW; ++j) {
+        kD[j] = tk.kd[kI[j]];
+        kA[j] = tk.ka[kI[j]];
+        kT[j] = tk.kt[kI[j]];
+      }
     }
     const T* __restrict__ Vo = static_cast<const T*>(a.Vt[(kk - 1) & 1]);
     T* __restrict__ Vn = static_cast<T*>(a.Vt[kk & 1]);
@@ -943,13 +947,15 @@ __device__ __forceinline__ int series_run(const SolveArgs& a, Team& tm, SeriesSm
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
           // block b of the new V: -xi t_i/s times block b, plus alpha_i/s times block b-1 when b >= 2
-          T v = kD[j] * vo[j];
+          T v;
           if constexpr (sizeof(T) == 4) {
+            v = kD[j] * vo[j];
             if (kUp[j]) v = fma(kA[j], vp[j], v);
           } else {
-            if (kUp[j]) v = fma(kA[j], Vo[o + j - r], v);
+            v = tk.kd[kI[j]] * vo[j];
+            if (kUp[j]) v = fma(tk.ka[kI[j]], Vo[o + j - r], v);
           }
-          const T d = fma(acc[j], kT[j], v);
+          const T d = fma(acc[j], sizeof(T) == 4 ? kT[j] : tk.kt[kI[j]], v);
           const T sn = sv[j] + d;
           vn[j] = kLive[j] ? v : T(0);
           dn[j] = kLive[j] ? d : T(0);
