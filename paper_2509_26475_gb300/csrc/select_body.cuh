@@ -118,7 +118,7 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
 struct SelShared {
   double lz[kLowRankMaxK];  // z = W^T x of a low-rank operator
   double L[kMaxM + 1];
-  double coef[kMaxM + 1];
+  alignas(16) double coef[kMaxM + 1];  // read in pairs (16-byte loads) by the objective pass
   double binom[kMaxM + 1];
   double lmax, gmax, gmin, s0, inv_s0, nv, fval;
   int r, go, status;
@@ -169,6 +169,70 @@ __device__ __forceinline__ Ssq gather_chunks(const Ssq* part, int parity, int n)
 // pass loads V_{2j} and V_{2j+1} of a row with one 16-byte load.
 __device__ __forceinline__ size_t vidx(int k, int n, long long row) {
   return ((size_t)(k >> 1) * n + (size_t)row) * 2 + (k & 1);
+}
+
+// One evaluation of the objective's sum of squares: y(row) = sum_k coef_k V_k[row] (k ascending) for every
+// row of this member's chunks, each chunk's scaled sum of squares of y into part[parity][chunk].  The
+// rows, their order and every rounding are those of chunk_pass over the same y; the thread's kChunk/kBlock
+// rows of a chunk are formed together, so that each coefficient pair is read from shared memory once (one
+// 16-byte load) for all of them.  On GB300 memory instructions share the FP64 pipe's issue path: one row
+// at a time took a 16-byte basis load and two 8-byte coefficient loads per two FMAs.
+__device__ __forceinline__ void objective_pass(int n, int m, const Team& tm, Ssq* part, int parity,
+                                               const double* __restrict__ Vb, const double* coef) {
+  constexpr int U = kChunk / kBlock;
+  const int nch = chunk_count(n);
+  const int pairs = (m + 1) >> 1;
+  const double2* __restrict__ Vp2 = reinterpret_cast<const double2*>(Vb);
+  const double2* cp = reinterpret_cast<const double2*>(coef);
+  for (int c = tm.rank; c < nch; c += tm.size) {
+    double y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) y[u] = 0.0;
+    const long long row0 = (long long)c * kChunk + threadIdx.x;
+    if (row0 + (U - 1) * kBlock < n) {  // every row of the thread in range (all chunks but a ragged last)
+      for (int jj = 0; jj < pairs; ++jj) {
+        const double2 cc = cp[jj];
+        double2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = Vp2[(size_t)jj * n + (size_t)(row0 + u * kBlock)];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          y[u] = fma(cc.x, v[u].x, y[u]);
+          y[u] = fma(cc.y, v[u].y, y[u]);
+        }
+      }
+      if ((m + 1) & 1) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) y[u] = fma(coef[m], Vb[vidx(m, n, row0 + u * kBlock)], y[u]);
+      }
+    } else {
+      for (int jj = 0; jj < pairs; ++jj) {
+        const double2 cc = cp[jj];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long long row = row0 + u * kBlock;
+          if (row < n) {
+            const double2 v = Vp2[(size_t)jj * n + (size_t)row];
+            y[u] = fma(cc.x, v.x, y[u]);
+            y[u] = fma(cc.y, v.y, y[u]);
+          }
+        }
+      }
+      if ((m + 1) & 1) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long long row = row0 + u * kBlock;
+          if (row < n) y[u] = fma(coef[m], Vb[vidx(m, n, row)], y[u]);
+        }
+      }
+    }
+    Ssq acc = ssq_empty();
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (row0 + u * kBlock < n) ssq_add(acc, y[u]);
+    const Ssq blk = block_ssq(acc);
+    if (threadIdx.x == 0) part[(size_t)parity * nch + c] = blk;
+  }
 }
 
 // (A x)[row] for the basis vector x = V_k (pair-interleaved, stride 2).
@@ -361,18 +425,7 @@ __device__ __forceinline__ void select_body(const SelectArgs& a, Team& tm, SelSh
       sh.coef[kk] = objective_coef(sh.binom[kk], -sh.br.u / sh.s0, m - kk);
     }
     __syncthreads();
-    const double2* __restrict__ Vp2 = reinterpret_cast<const double2*>(a.Vb);
-    const int pairs = (m + 1) >> 1;
-    chunk_pass(n, tm, part, pc & 1, [&](long long row) {
-      double y = 0.0;
-      for (int jj = 0; jj < pairs; ++jj) {  // y = sum_k coef_k V_k[row], k ascending
-        const double2 v = Vp2[(size_t)jj * n + row];
-        y = fma(sh.coef[2 * jj], v.x, y);
-        y = fma(sh.coef[2 * jj + 1], v.y, y);
-      }
-      if ((m + 1) & 1) y = fma(sh.coef[m], a.Vb[vidx(m, n, row)], y);
-      return y;
-    });
+    objective_pass(n, m, tm, part, pc & 1, a.Vb, sh.coef);  // y = sum_k coef_k V_k[row], k ascending
     if (!team_sync(tm)) return;
     const Ssq tot = gather_chunks(part, pc & 1, n);
     ++pc;
