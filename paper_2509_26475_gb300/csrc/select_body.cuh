@@ -190,7 +190,25 @@ __device__ __forceinline__ void objective_pass(int n, int m, const Team& tm, Ssq
     for (int u = 0; u < U; ++u) y[u] = 0.0;
     const long long row0 = (long long)c * kChunk + threadIdx.x;
     if (row0 + (U - 1) * kBlock < n) {  // every row of the thread in range (all chunks but a ragged last)
-      for (int jj = 0; jj < pairs; ++jj) {
+      // two pairs of basis vectors a step: 2 U independent 16-byte loads in flight a thread
+      int jj = 0;
+      for (; jj + 1 < pairs; jj += 2) {
+        const double2 c0 = cp[jj], c1 = cp[jj + 1];
+        double2 v0[U], v1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          v0[u] = Vp2[(size_t)jj * n + (size_t)(row0 + u * kBlock)];
+          v1[u] = Vp2[(size_t)(jj + 1) * n + (size_t)(row0 + u * kBlock)];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          y[u] = fma(c0.x, v0[u].x, y[u]);
+          y[u] = fma(c0.y, v0[u].y, y[u]);
+          y[u] = fma(c1.x, v1[u].x, y[u]);
+          y[u] = fma(c1.y, v1[u].y, y[u]);
+        }
+      }
+      if (jj < pairs) {
         const double2 cc = cp[jj];
         double2 v[U];
 #pragma unroll
