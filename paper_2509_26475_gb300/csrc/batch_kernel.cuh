@@ -41,12 +41,16 @@ __device__ __noinline__ void select_call(const SelectArgs& a, Team& tm, SelShare
 
 template <typename T>
 __device__ __forceinline__ void run_series(const SolveArgs& a, Team& tm, BatchSmem& u, int& phase);
-// Lane widths follow pick_layout: FP64 tiles take 1 or 2 columns per lane up to 32 columns and 4
-// beyond; FP32 tiles 1, 2, 4 or 8.
+// Lane widths follow pick_layout: FP64 tiles take 1, 2 or 4 columns per lane, FP32 tiles 1, 2, 4 or 8,
+// and FP64 series tiles whose width divides by 3 or 5 that many where it leaves no idle lanes (batched
+// and served FP32 instances keep the power-of-two lanes: two more bodies per kernel took the build of
+// each batched translation unit from 85 to 136 s, for lanes that are not bound by the FP64 pipe).
 template <>
 __device__ __forceinline__ void run_series<double>(const SolveArgs& a, Team& tm, BatchSmem& u, int& phase) {
   if (a.S_lay.cw == 1) series_call<double, 1>(a, tm, u.s64, phase);
   else if (a.S_lay.cw == 2) series_call<double, 2>(a, tm, u.s64, phase);
+  else if (a.S_lay.cw == 3) series_call<double, 3>(a, tm, u.s64, phase);
+  else if (a.S_lay.cw == 5) series_call<double, 5>(a, tm, u.s64, phase);
   else series_call<double, 4>(a, tm, u.s64, phase);
 }
 template <>

@@ -85,7 +85,7 @@ bool make_layout(const phic_batch_item* items, int count, const phic_select_opts
     }
     il.solve_off = off;
     if (il.do_solve) {
-      il.sl = solve_layout(it.A.n, it.A.nnz, it.p, it.r, it.A.prec);
+      il.sl = solve_layout(it.A.n, it.A.nnz, it.p, it.r, it.A.prec, it.A.prec == PHIC_F64);
       off += il.sl.total;
     }
   }

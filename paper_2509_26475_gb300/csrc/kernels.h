@@ -15,8 +15,8 @@ struct Ctl;
 struct TileLayout {
   int w, ws, cw, L, Lp2;
 };
-// odd_cw: FP64 tiles may also take 3 or 5 columns a lane where that leaves fewer idle lanes (only the
-// single-instance series kernels are built for those widths).
+// odd_cw: tiles may also take 3 or 5 columns a lane where that leaves fewer idle lanes (only for series
+// kernels built for those widths; see solve_layout).
 TileLayout pick_layout(int w, int elem_bytes, bool odd_cw = false);
 
 // Per-solve loop state in device memory.  The series writes the first block; the recovery reads it and,

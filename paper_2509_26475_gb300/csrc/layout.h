@@ -46,12 +46,12 @@ struct SolveLayout {
   long long a1_cap;
   TileLayout sl, fl;
 };
-// single: the layout of the single-instance solve (phic_solve and its workspace query), whose series
-// kernels also exist for FP64 tiles of 3 and 5 columns a lane.
-inline SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec, bool single = false) {
+// odd_cw: the series tile may take 3 or 5 columns a lane (pick_layout); the single-instance series is built
+// for those widths, the batched one for FP64 tiles only, the low-rank one not at all.
+inline SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec, bool odd_cw = false) {
   SolveLayout L;
   const size_t es = prec == PHIC_F32 ? 4 : 8;
-  L.sl = pick_layout((p + 1) * r, (int)es, single);
+  L.sl = pick_layout((p + 1) * r, (int)es, odd_cw);
   L.fl = pick_layout(p == 0 ? r : 2 * r, (int)es);
   const size_t tileS = align_up((size_t)n * L.sl.ws * es);
   const size_t tileF = align_up((size_t)n * L.fl.ws * es);

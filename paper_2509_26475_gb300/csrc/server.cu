@@ -134,7 +134,7 @@ void plan_blocks(Req& q, int m) {
     q.o_V = off; off += align_up((size_t)q.vrows() * n * q.es);
     q.o_W = off; off += align_up((size_t)q.r.r * n * q.es);
     q.o_stats = off; off += align_up(sizeof(phic_stats));
-    q.sl = solve_layout(n, nnz, q.r.p, q.r.r, q.r.prec);
+    q.sl = solve_layout(n, nnz, q.r.p, q.r.r, q.r.prec, q.r.prec == PHIC_F64);
     q.o_solve = off; off += q.sl.total;
   }
   q.bytes_main = off;
