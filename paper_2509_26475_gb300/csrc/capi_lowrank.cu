@@ -67,7 +67,7 @@ phic_status phic_lowrank_solve_workspace_size(int64_t n, int32_t k, int32_t p, i
   if (!bytes || n < 1 || n >= (int64_t)INT32_MAX || k < 1 || k > PHIC_MAX_RANK || p < 0 || p > PHIC_MAX_P || r < 1 ||
       r > PHIC_MAX_R || (p + 1) * r * k > kLowRankMaxE || (prec != PHIC_F64 && prec != PHIC_F32))
     return PHIC_INVALID_ARG;
-  *bytes = solve_layout(n, 0, p, r, prec).total + lr_part_bytes(k, (p + 1) * r);
+  *bytes = solve_layout(n, 0, p, r, prec, prec == PHIC_F64).total + lr_part_bytes(k, (p + 1) * r);
   return PHIC_OK;
 }
 
@@ -82,7 +82,7 @@ phic_status phic_lowrank_solve(const phic_lowrank* A, int32_t p, int32_t r, cons
   if (!solve_args_ok(&c_chk, p, r, V, t, alpha, tol, flags, PHIC_NO_V0, prec) || !W || !params_dev || !ws ||
       !aligned(ws) || (p + 1) * r * A->k > kLowRankMaxE)
     return PHIC_INVALID_ARG;
-  const SolveLayout L = solve_layout(A->n, 0, p, r, prec);
+  const SolveLayout L = solve_layout(A->n, 0, p, r, prec, prec == PHIC_F64);
   if (ws_bytes < L.total + lr_part_bytes(A->k, (p + 1) * r)) return PHIC_WORKSPACE_TOO_SMALL;
   char* base = static_cast<char*>(ws);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

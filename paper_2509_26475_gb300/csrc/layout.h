@@ -47,7 +47,7 @@ struct SolveLayout {
   TileLayout sl, fl;
 };
 // odd_cw: the series tile may take 3 or 5 columns a lane (pick_layout); the single-instance series is built
-// for those widths, the batched one for FP64 tiles only, the low-rank one not at all.
+// for those widths, the batched and the low-rank ones for FP64 tiles only.
 inline SolveLayout solve_layout(int64_t n, int64_t nnz, int p, int r, int prec, bool odd_cw = false) {
   SolveLayout L;
   const size_t es = prec == PHIC_F32 ? 4 : 8;

@@ -81,6 +81,13 @@ cudaError_t dispatch_lr_series(const SolveArgs& a, cudaStream_t st) {
   switch (a.S_lay.cw) {
     case 1: return coop_launch(lr_series_kernel<T, 1>, items, bps, a, st, nullptr, kLowRankMaxGrid);
     case 2: return coop_launch(lr_series_kernel<T, 2>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+    case 3:
+    case 5:  // FP64 tiles whose width divides by 3 or 5 (solve_layout)
+      if constexpr (sizeof(T) == 8) {
+        if (a.S_lay.cw == 3) return coop_launch(lr_series_kernel<T, 3>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+        return coop_launch(lr_series_kernel<T, 5>, items, bps, a, st, nullptr, kLowRankMaxGrid);
+      }
+      return cudaErrorInvalidValue;
 #if PHIC_CW_MAX_F32 >= 8
     case 8:
       if constexpr (sizeof(T) == 4) return coop_launch(lr_series_kernel<T, 8>, items, bps, a, st, nullptr, kLowRankMaxGrid);
