@@ -151,6 +151,18 @@ phic_status phic_params_set(phic_params* params_dev, double xi, double s, phic_s
  * control blocks. */
 phic_status phic_solve_workspace_size(int64_t n, int64_t nnz, int32_t p, int32_t r, int32_t prec, size_t* bytes);
 
+/* The lane layout the solve kernels give a row-major block tile of w columns (a host query; no device
+ * work).  Algorithm 3's series carries the (p+1) r columns of its block series, the recovery the 2r (r when
+ * p = 0) columns of F.  Each row is handled by L lanes of cw columns, grouped into Lp2 (the next power of
+ * two >= L) consecutive lanes; idle lanes of a group cost their warp's instructions all the same.  odd_cw != 0
+ * allows 3 or 5 columns a lane where that leaves fewer lane slots (Lp2 cw) than the power-of-two widths,
+ * as phic_solve does for its series tile.
+ *   w       columns, 1 .. PHIC_MAX_WIDTH
+ *   prec    PHIC_F64 or PHIC_F32
+ *   out     host int32[5]: {w, the tile's row stride ws (elements), cw, L, Lp2}
+ * Returns PHIC_INVALID_ARG for any other w or prec, or a null out. */
+phic_status phic_tile_layout(int32_t w, int32_t prec, int32_t odd_cw, int32_t* out);
+
 /* Algorithm 3 (Section 4): w_i = sum_j alpha_i^j phi_j(t_i A) v_j for i = 1..r.
  *   A       CSR operator; A->prec must equal `prec`.
  *   p, r    0 <= p <= PHIC_MAX_P, 1 <= r <= PHIC_MAX_R, (p+1) r <= PHIC_MAX_WIDTH.

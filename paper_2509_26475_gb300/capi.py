@@ -140,6 +140,7 @@ SIGNATURES = [
     ("phic_params_set", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P]),
     ("phic_solve_workspace_size", ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    ("phic_tile_layout", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     ("phic_solve", ctypes.c_int, [ctypes.POINTER(phic_csr), ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
                                   ctypes.c_double, _P, ctypes.c_uint32, ctypes.c_int32, _P, _P, ctypes.c_size_t, _P,
                                   ctypes.c_int32, _P]),

@@ -82,6 +82,17 @@ phic_status phic_solve_workspace_size(int64_t n, int64_t nnz, int32_t p, int32_t
   return PHIC_OK;
 }
 
+phic_status phic_tile_layout(int32_t w, int32_t prec, int32_t odd_cw, int32_t* out) {
+  if (!out || w < 1 || w > PHIC_MAX_WIDTH || (prec != PHIC_F64 && prec != PHIC_F32)) return PHIC_INVALID_ARG;
+  const TileLayout t = pick_layout(w, prec == PHIC_F32 ? 4 : 8, odd_cw != 0);
+  out[0] = t.w;
+  out[1] = t.ws;
+  out[2] = t.cw;
+  out[3] = t.L;
+  out[4] = t.Lp2;
+  return PHIC_OK;
+}
+
 phic_status phic_solve(const phic_csr* A, int32_t p, int32_t r, const void* V, const double* t, const double* alpha,
                        double tol, const phic_params* params_dev, uint32_t flags, int32_t max_terms, void* W, void* ws,
                        size_t ws_bytes, phic_stats* stats_dev, int32_t prec, phic_stream_t stream) {
